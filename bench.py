@@ -1,0 +1,369 @@
+"""Benchmark: Gaussian pair x point potential evaluations per second.
+
+One step = one esp_eval_walkers call over one batch of walker positions (all
+of the path: staging, the potential kernel over every distribution and point
+charge, the partial-sum reduction, the per-walker energy reduction).
+
+Workload (default): the realistic environment, 2,000 atoms on a jittered
+2.8 bohr lattice outside the 6 bohr QM sphere with cc-pVDZ-shaped primitives
+and a local PSD density (~1.1e6 Hermite distributions after screening at
+1e-12) plus 2,000 nuclei, evaluated at 4,096 walkers x 32 electrons = 131,072
+positions per GPU per step.  One eval = one distribution (or point charge) x
+one position.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank evaluates its own walkers against the same
+environment (weak scaling, no collective on the data path); rank 0 prints one
+JSON line.  `--impl reference` times the FP64 CPU oracle on this host's cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gaussian pair×point potential evals/s at ≤1e-5 Ha: FP64 vs FP32 vs surrogate"
+
+# FP32 operations per evaluation by total angular momentum L (see the design doc:
+# offset 3, |r|^2 3, scaled offset 3, T 1-3, Boys 2+2L, Hermite recursion and
+# contraction, accumulate 1).  MUFU work (one rsqrt) is not counted.
+OPS_PER_EVAL = {0: 10, 1: 26, 2: 52, 3: 95, 4: 170}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def keep_heap():
+    try:
+        import ctypes
+        libc = ctypes.CDLL("libc.so.6")
+        libc.mallopt(-4, 0)
+        libc.mallopt(-1, 1 << 30)
+    except (OSError, AttributeError):
+        pass
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("esp_kernels.cu", "esp_internal.h"):
+        with open(os.path.join(ROOT, "paper_1011_4687_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, units: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `units`
+    (positions x evals) — None if the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_launch"] * units / e["units_per_launch"]
+
+
+def build_workload(rank: int):
+    from workloads import realistic_environment, seed_for_config, qm_positions
+    wl = realistic_environment(seed=seed_for_config(2))
+    if rank > 0:
+        rng = np.random.default_rng(seed_for_config(2) * 1000 + rank)
+        wl.positions = qm_positions(rng, wl.n_walkers * wl.n_elec)
+    return wl
+
+
+def sample_indices(wl):
+    """Two whole walkers and the 32 positions closest to the environment."""
+    r = np.linalg.norm(wl.positions, axis=1)
+    outer = np.argsort(-r)[:32]
+    ws = [0, wl.n_walkers - 1]
+    return ws, np.concatenate([np.arange(w * wl.n_elec, (w + 1) * wl.n_elec) for w in ws] + [outer])
+
+
+def run_reference(args):
+    """The oracle as it stands, on this host's cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    wl = build_workload(0)
+    n_units = (wl.meta["n_shell_pairs"] + wl.nuclei_Z.size)
+    sample = np.arange(args.ref_positions)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions[sample])
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    per = statistics.mean(times)
+    val = n_units * sample.size / per
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "distributions": wl.meta["n_shell_pairs"],
+                       "point_charges": int(wl.nuclei_Z.size), "positions_per_step": int(sample.size)},
+            "cpu_baseline": {"value": val, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "%d positions of the realistic workload per step (all distributions)"
+                                       % sample.size},
+            "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-walkers", type=int, default=256, help="walkers in the FP64 rate measurement")
+    ap.add_argument("--ref-positions", type=int, default=32, help="positions per oracle step (reference arm)")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
+    args = ap.parse_args(argv)
+    keep_heap()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1011_4687_gb300 import build_lib, esp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    esp.load()
+
+    wl = build_workload(rank)
+    stream = torch.cuda.current_stream()
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
+    info = env.info()
+    n_pos = wl.n_positions
+    units_per_pos = info["n_distributions"] + info["n_point_charges"]
+    evals_per_step = units_per_pos * n_pos
+    pos = torch.from_numpy(wl.positions).cuda()
+    V = torch.empty(n_pos, dtype=torch.float64, device="cuda")
+    E = torch.empty(wl.n_walkers, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    env.set_timing(True)
+    for _ in range(args.warmup):
+        env.eval_walkers(pos, wl.n_walkers, wl.n_elec, V_out=V, E_out=E)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            env.eval_walkers(pos, wl.n_walkers, wl.n_elec, V_out=V, E_out=E)
+            ends[k].record(stream)
+            kern_ms.append(env.last_timing()[0])
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    t_rank = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+    ms_max = float(t_rank.item())
+    value = evals_per_step * world / (ms_max * 1e-3)
+    kern = statistics.mean(kern_ms)
+    clocks = clk.summary()
+
+    # end to end through the public API with pinned host buffers
+    pin_pos = torch.from_numpy(wl.positions).pin_memory()
+    pin_V = torch.empty(n_pos, dtype=torch.float64).pin_memory()
+    pin_E = torch.empty(wl.n_walkers, dtype=torch.float64).pin_memory()
+    hp, hv, he = pin_pos.numpy(), pin_V.numpy(), pin_E.numpy()
+    env.eval_walkers(hp, wl.n_walkers, wl.n_elec, V_out=hv, E_out=he)
+    e2e_t = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        env.eval_walkers(hp, wl.n_walkers, wl.n_elec, V_out=hv, E_out=he)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = evals_per_step * world / statistics.mean(e2e_t)
+
+    # FP64 rate on a subset of walkers (same environment, same kernels' FP64 variant)
+    nw64 = min(args.fp64_walkers, wl.n_walkers)
+    pos64 = pos[: nw64 * wl.n_elec].contiguous()
+    env.set_precision("fp64")
+    env.eval_walkers(pos64, nw64, wl.n_elec)
+    torch.cuda.synchronize()
+    f64 = []
+    for _ in range(2):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        env.eval_walkers(pos64, nw64, wl.n_elec)
+        s1.record(stream)
+        s1.synchronize()
+        f64.append(s0.elapsed_time(s1))
+    fp64_val = units_per_pos * nw64 * wl.n_elec / (statistics.mean(f64) * 1e-3)
+    env.set_precision("fp32c")
+
+    if rank != 0:
+        env.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the potential kernel (FP32 issue bound)
+    peaks, peak_src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6
+    ops_launch = n_pos * sum(OPS_PER_EVAL[L] * info["n_by_L"][L] for L in range(5))
+    achieved = ops_launch / (kern * 1e-3)
+    traffic = profiled_traffic("potential_f32c_kernel", float(evals_per_step))
+
+    out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "realistic: 2,000 atoms, cc-pVDZ-shaped primitives, %d distributions + "
+                                  "%d point charges, %d positions (%d walkers x %d electrons) per GPU"
+                                  % (info["n_distributions"], info["n_point_charges"], n_pos, wl.n_walkers,
+                                     wl.n_elec),
+                      "precision": "FP32C (FP32 pair sum, compensated; nuclei and near blocks FP64)",
+                      "distributions_by_L": info["n_by_L"], "evals_per_step_per_gpu": evals_per_step,
+                      "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas" if world > 1 else "single"},
+           "gpu_launches": 4 * args.steps,
+           "clocks": clocks,
+           "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                        "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": traffic,
+                        "kernel": "potential_f32c_kernel", "kernel_ms": kern,
+                        "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_src)},
+           "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": int(n_pos * 24),
+                   "d2h_bytes_per_step": int(n_pos * 8 + wl.n_walkers * 8)},
+           "fp64": {"value": fp64_val, "unit": "evals/s", "positions_per_step": nw64 * wl.n_elec,
+                    "ms_per_step": statistics.mean(f64)}}
+
+    if not args.no_oracle:
+        import oracle
+        oracle.build()
+        ws, sample = sample_indices(wl)
+        t0 = time.perf_counter()
+        ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions[sample])
+        t_or = time.perf_counter() - t0
+        Vs = V.cpu().numpy()[sample]
+        Es = E.cpu().numpy()[ws]
+        Eref = oracle.walker_energies(ref[: 2 * wl.n_elec], 2, wl.n_elec)
+        env.set_precision("fp64")
+        V64 = env.eval(torch.from_numpy(wl.positions[sample]).cuda())
+        torch.cuda.synchronize()
+        V64 = V64.cpu().numpy()
+        out["accuracy"] = {"sample": "2 whole walkers + 32 outermost positions",
+                           "fp32c_max_point_err_ha": float(np.abs(Vs - ref).max()),
+                           "fp32c_max_walker_err_ha": float(np.abs(Es - Eref).max()),
+                           "fp64_max_rel_err": float(np.max(np.abs(V64 - ref) / np.maximum(np.abs(ref), 1.0)))}
+        out["cpu_baseline"] = {"value": units_per_pos * sample.size / t_or, "unit": "evals/s",
+                               "cores": oracle.max_threads(), "kind": "oracle",
+                               "sample": "%d positions x all %d distributions + point charges"
+                                         % (sample.size, units_per_pos)}
+    env.close()
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,211 @@
+/*
+ * esp.h — C ABI of the GB300 environment-electrostatic-potential library.
+ *
+ * The library evaluates, at many electron positions C, the electrostatic
+ * potential of a fixed QM/MM environment:
+ *
+ *   V(C) = sum_beta Z_beta / |C - R_beta|                       (point charges)
+ *        + sum_ab w_ab * int chi_a(r) chi_b(r) / |r - C| dr     (Gaussian pairs)
+ *
+ * with chi(r) = (x-Ax)^i (y-Ay)^j (z-Az)^k exp(-alpha |r-A|^2) an
+ * unnormalised Cartesian primitive.  This is the field of Eq.
+ * ElectrostaticField (Sec. II.B of "Acceleration of a QM/MM-QMC simulation
+ * using GPU"), U_ES(r_new) = sum_m rho(r_m)/|r_new - r_m| - sum_beta
+ * Z_beta/|r_new - R_beta|, with U_ES = -V for an electron: the paper's
+ * discretised cells rho(r_m) are point charges of value -rho (pass them as
+ * point charges), and a density given in a Gaussian basis is passed as
+ * weighted primitive pairs.  Units: bohr in, hartree per elementary charge out.
+ *
+ * The split between esp_create (environment uploaded once, read-only on the
+ * device) and esp_eval (positions in, potentials out, every Monte Carlo step)
+ * follows the paper's data-residency design (Sec. III: the cell data is sent
+ * to the GPU once; per step only r_new goes in and U_ES comes out).
+ *
+ * Conventions for every entry point:
+ *  - No exception crosses the ABI and nothing aborts.  A failing call returns
+ *    a non-zero esp_status and leaves its outputs untouched (for device
+ *    outputs: not written by any kernel of this call); esp_last_error() then
+ *    holds a one-line message for the calling thread.
+ *  - Pointers named "host or device" may point to host memory (pageable or
+ *    pinned) or to device memory of the context's device; all arrays passed
+ *    to one call must live in the same space.  With host pointers the call is
+ *    synchronous.  With device pointers the work is enqueued on the context's
+ *    stream and the call returns without synchronising; the caller orders
+ *    later reads on that stream or calls esp_synchronize.
+ *  - The library copies every input it keeps; the caller may free its arrays
+ *    as soon as a call returns (device inputs: once the stream has passed the
+ *    call).
+ *  - One context may be used by one host thread at a time; a call that finds
+ *    the context busy returns ESP_ERR_STATE.
+ */
+#ifndef ESP_H
+#define ESP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESP_ABI_VERSION 1
+#define ESP_MAX_L 4 /* largest la + lb of one primitive pair */
+
+/* esp_options.flags: build the tiles on the host only, touch no GPU.  Such a
+ * context serves esp_get_info and esp_debug_host_eval (test hooks); every
+ * evaluation call on it returns ESP_ERR_STATE. */
+#define ESP_FLAG_HOST_ONLY 1
+
+typedef struct esp_ctx esp_ctx;
+
+typedef enum {
+    ESP_OK = 0,
+    ESP_ERR_INVALID = 1,     /* bad argument: null pointer, non-finite value, exponent <= 0,
+                                negative or too large angular momentum, n < 0, wrong memory space */
+    ESP_ERR_OOM = 2,         /* a host or device allocation failed */
+    ESP_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in esp_last_error) */
+    ESP_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out; the context stays usable */
+    ESP_ERR_STATE = 5,       /* context busy in another thread, or destroyed */
+    ESP_ERR_UNSUPPORTED = 6  /* valid request this build does not handle */
+} esp_status;
+
+/* A point charge: nucleus (Z > 0) or a discretised density cell (charge -rho).
+ * Sec. II.B, Eq. ElectrostaticField: {Z_beta, R_beta} and {rho(r_m), r_m}. */
+typedef struct {
+    double xyz[3];
+    double Z;
+} esp_point_charge;
+
+/* One product of two unnormalised Cartesian primitives (96 bytes).  lmn_a and
+ * lmn_b are the Cartesian exponents (i, j, k); la + lb <= ESP_MAX_L where
+ * la = i+j+k of A.  The density weight of the pair is passed separately. */
+typedef struct {
+    double A[3];
+    double alpha;
+    int32_t lmn_a[3];
+    int32_t pad_a;
+    double B[3];
+    double beta;
+    int32_t lmn_b[3];
+    int32_t pad_b;
+} esp_gauss_pair;
+
+typedef enum {
+    ESP_FP64 = 0,  /* every step in FP64: reference-accuracy path */
+    ESP_FP32C = 1  /* bulk of the pair sum in FP32 with compensated accumulation;
+                      point charges and near (position, tile) blocks in FP64 */
+} esp_precision;
+
+typedef struct {
+    int32_t size;                  /* sizeof(esp_options); filled by esp_default_options */
+    int32_t precision;             /* esp_precision; default ESP_FP32C */
+    double screen_tol;             /* drop distributions whose absolute charge bound is below
+                                      this; default 1e-12; 0 keeps every pair */
+    double qm_center[3];           /* positions and centres are recentred here in FP64 */
+    void *cuda_stream;             /* cudaStream_t for all work; NULL = the default stream */
+    int32_t device;                /* CUDA device ordinal; -1 = the current device */
+    int32_t tile_size;             /* distributions per tile: 64, 128 or 256; 0 = 128 */
+    int32_t threads_per_block;     /* 0 = tuned default */
+    int32_t positions_per_thread;  /* 0 = tuned default */
+    int32_t pair_splits;           /* tiles are dealt round-robin to this many splits per
+                                      position block; 0 = chosen from the problem size */
+    int32_t flags;                 /* ESP_FLAG_* bits; 0 for normal use */
+    double near_radius;            /* FP32C: a (position, tile) block whose distance to the
+                                      tile's bounding sphere is below this is evaluated in
+                                      FP64; < 0 = default (1.5 bohr) */
+} esp_options;
+
+/* Per-context facts, for reporting and for counting evaluations. */
+typedef struct {
+    int64_t n_point_charges;       /* point charges kept */
+    int64_t n_pairs_in;            /* primitive pairs passed to esp_create */
+    int64_t n_distributions;       /* Hermite distributions after folding and screening */
+    int64_t n_screened;            /* distributions dropped by screen_tol */
+    int64_t n_by_L[ESP_MAX_L + 1]; /* distributions per total angular momentum L */
+    int64_t n_tiles;               /* tiles of distributions and of point charges */
+    int64_t device_bytes;          /* device memory held by the context */
+    int32_t precision;
+    int32_t tile_size;
+    int32_t threads_per_block;
+    int32_t positions_per_thread;
+    int32_t pair_splits;
+    int32_t device;
+} esp_info;
+
+/* Fill *opt with defaults (FP32C, screen 1e-12, centre origin, default stream,
+ * current device, tuned launch shape). */
+void esp_default_options(esp_options *opt);
+
+/* Build a context: validate, fold pairs that share (A, alpha, B, beta) into one
+ * Hermite distribution (McMurchie-Davidson expansion), screen, sort into tiles
+ * and upload once (Sec. III, data residency).
+ *   charges [n_charges]   host; may be NULL when n_charges == 0
+ *   pairs   [n_pairs]     host; may be NULL when n_pairs == 0
+ *   weights [n_pairs]     host; density weight w_ab of each pair
+ *   opt                   NULL = defaults
+ *   out                   receives the context; untouched on error
+ * Errors: ESP_ERR_INVALID (bad input), ESP_ERR_OOM, ESP_ERR_CUDA. */
+esp_status esp_create(const esp_point_charge *charges, int64_t n_charges,
+                      const esp_gauss_pair *pairs, const double *weights, int64_t n_pairs,
+                      const esp_options *opt, esp_ctx **out);
+
+/* V[i] = potential at positions[i] (Eq. ElectrostaticField with U_ES = -V).
+ *   positions [n][3] host or device, float64, row-major
+ *   V_out     [n]    same space as positions, float64
+ * n == 0 is a no-op.  Errors: ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_CUDA,
+ * ESP_ERR_TIMEOUT, ESP_ERR_OOM. */
+esp_status esp_eval(esp_ctx *ctx, const double *positions, int64_t n, double *V_out);
+
+/* Walker-major positions [n_walkers][n_elec][3]; E_out[w] = sum_e U_ES(r_we) =
+ * -sum_e V(r_we), reduced in FP64 on the device in a fixed order.  V_out may
+ * be NULL.  Same memory-space rules as esp_eval. */
+esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_walkers,
+                            int64_t n_elec, double *V_out, double *E_out);
+
+/* Switch the arithmetic of later evaluations (ESP_FP64 or ESP_FP32C). */
+esp_status esp_set_precision(esp_ctx *ctx, int32_t precision);
+
+/* Fill *info.  Errors: ESP_ERR_INVALID. */
+esp_status esp_get_info(const esp_ctx *ctx, esp_info *info);
+
+/* Kernel timing.  With enable != 0, each later evaluation records CUDA events
+ * on the context's stream around its potential kernel (the Eq.
+ * ElectrostaticField sum) and around the whole device pipeline (staging,
+ * potential, reductions).  esp_last_timing waits for the last evaluation and
+ * returns both durations in milliseconds.  Errors: ESP_ERR_STATE when timing
+ * is off or nothing was evaluated since it was enabled. */
+esp_status esp_set_timing(esp_ctx *ctx, int32_t enable);
+esp_status esp_last_timing(esp_ctx *ctx, double *potential_ms, double *pipeline_ms);
+
+/* Wait for the context's stream. */
+esp_status esp_synchronize(esp_ctx *ctx);
+
+/* Free every resource of ctx.  NULL is a no-op. */
+void esp_destroy(esp_ctx *ctx);
+
+/* Static English name of a status code. */
+const char *esp_status_string(esp_status s);
+
+/* Message of the last failing call in this host thread ("" if none). */
+const char *esp_last_error(void);
+
+/* ABI version of the loaded library (ESP_ABI_VERSION). */
+int32_t esp_abi_version(void);
+
+/* Test hook, not part of the evaluation path: evaluate the Boys function
+ * F_0..F_nmax(T) with the device algorithm of the given precision, run on the
+ * host (nmax <= ESP_MAX_L).  Lets CPU tests check the tables and the Taylor
+ * and asymptotic branches without a GPU. */
+esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_out);
+
+/* Test hook, not part of the evaluation path: evaluate a built context's
+ * tiles on the host in FP64 with the device's Hermite code, so CPU tests can
+ * check folding, screening and tiling of the pair builder.  positions and
+ * V_out are host arrays.  esp_eval never calls this. */
+esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int64_t n,
+                               double *V_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESP_H */

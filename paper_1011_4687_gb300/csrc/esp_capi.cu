@@ -1,0 +1,660 @@
+// C ABI of the library (declared in include/esp.h).
+//
+// Data residency follows the paper (Sec. III): the environment is built and
+// uploaded once by esp_create and stays read-only on the device; each
+// esp_eval moves only positions in and potentials out.  Device scratch
+// (staged positions, per-split partial sums) is owned by the context and
+// grows on demand.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/esp.h"
+#include "esp_kernels.h"
+#include "pair_builder.h"
+
+using namespace esp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+esp_status fail(esp_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+esp_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(ESP_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(ESP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release()
+    {
+        if (p)
+            cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t need)
+    {
+        if (need <= bytes)
+            return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = need;
+        return cudaSuccess;
+    }
+};
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess)
+            ok = true;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+struct BusyGuard {
+    std::atomic<int> &flag;
+    bool acquired;
+    explicit BusyGuard(std::atomic<int> &f) : flag(f)
+    {
+        int expect = 0;
+        acquired = flag.compare_exchange_strong(expect, 1);
+    }
+    ~BusyGuard()
+    {
+        if (acquired)
+            flag.store(0);
+    }
+};
+
+} // namespace
+
+struct esp_ctx {
+    int device = 0;
+    int num_sms = 152;
+    cudaStream_t stream = nullptr;
+    esp_options opt;
+    HostEnv env;             // host copy of the tiles (kept for esp_get_info / test hook)
+    bool host_copy = true;
+    DevBuf tiles, rec32, rec64, boys32, boys64;
+    DevBuf in, stage, partial, vout, eout;
+    std::atomic<int> busy{0};
+    int64_t device_bytes = 0;
+    int n_tiles = 0;
+    int threads[2] = {128, 128};  // per precision (0 = FP64, 1 = FP32C)
+    int ppt[2] = {2, 4};
+    bool timing = false;
+    bool timed_valid = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr}; // pipeline start, kernel start/end, pipeline end
+    uint32_t magic = 0x45535021u;
+};
+
+namespace {
+
+bool valid_ctx(const esp_ctx *c) { return c && c->magic == 0x45535021u; }
+
+enum class Space { Host, Device, Invalid };
+
+Space classify(const void *p, int device)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return Space::Host;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return at.device == device ? Space::Device : Space::Invalid;
+    return Space::Host;
+}
+
+int choose_splits(const esp_ctx *c, int n, int prec)
+{
+    if (c->opt.pair_splits > 0)
+        return std::max(1, std::min(c->opt.pair_splits, std::max(c->n_tiles, 1)));
+    int per_cta = c->threads[prec] * c->ppt[prec];
+    int blocks = (n + per_cta - 1) / per_cta;
+    int target = 8 * c->num_sms;
+    int s = (target + blocks - 1) / blocks;
+    s = std::min(s, std::max(c->n_tiles, 1));
+    s = std::min(s, 1024);
+    return std::max(s, 1);
+}
+
+esp_status ensure_scratch(esp_ctx *c, int64_t n, int splits, bool host_io, int64_t n_walkers)
+{
+    cudaError_t e;
+    if (host_io && (e = c->in.ensure(size_t(n) * 3 * sizeof(double))) != cudaSuccess)
+        return cuda_fail(e, "allocating position staging");
+    if ((e = c->stage.ensure(size_t(n) * (3 * sizeof(double) + 6 * sizeof(float)) + 256)) != cudaSuccess)
+        return cuda_fail(e, "allocating staged positions");
+    if ((e = c->partial.ensure(size_t(n) * splits * sizeof(double))) != cudaSuccess)
+        return cuda_fail(e, "allocating partial sums");
+    if ((e = c->vout.ensure(size_t(n) * sizeof(double))) != cudaSuccess)
+        return cuda_fail(e, "allocating potentials");
+    if (n_walkers > 0 && (e = c->eout.ensure(size_t(n_walkers) * sizeof(double))) != cudaSuccess)
+        return cuda_fail(e, "allocating walker energies");
+    return ESP_OK;
+}
+
+Staged staged_view(esp_ctx *c, int64_t n)
+{
+    char *b = static_cast<char *>(c->stage.p);
+    Staged st;
+    st.x64 = reinterpret_cast<double *>(b);
+    st.y64 = st.x64 + n;
+    st.z64 = st.y64 + n;
+    float *f = reinterpret_cast<float *>(st.z64 + n);
+    st.xh = f;
+    st.yh = f + n;
+    st.zh = f + 2 * n;
+    st.xl = f + 3 * n;
+    st.yl = f + 4 * n;
+    st.zl = f + 5 * n;
+    return st;
+}
+
+// The evaluation pipeline shared by esp_eval and esp_eval_walkers.
+esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_out, int64_t n_walkers,
+                    int64_t n_elec, double *E_out)
+{
+    if (n < 0 || n > (int64_t(1) << 30))
+        return fail(ESP_ERR_INVALID, "position count %lld out of range", (long long)n);
+    if (n == 0)
+        return ESP_OK;
+    if (!positions || (!V_out && !E_out))
+        return fail(ESP_ERR_INVALID, "null positions or outputs");
+    BusyGuard busy(c->busy);
+    if (!busy.acquired)
+        return fail(ESP_ERR_STATE, "context is in use by another thread");
+    DeviceGuard dg(c->device);
+    if (!dg.ok)
+        return fail(ESP_ERR_CUDA, "cannot select device %d", c->device);
+    Space sp = classify(positions, c->device);
+    Space sv = V_out ? classify(V_out, c->device) : sp;
+    Space se = E_out ? classify(E_out, c->device) : sp;
+    if (sp == Space::Invalid || sv != sp || se != sp)
+        return fail(ESP_ERR_INVALID, "positions and outputs must all be host memory or all be device memory of "
+                                     "device %d", c->device);
+    const bool host_io = sp == Space::Host;
+    const int prec = c->opt.precision == ESP_FP64 ? 0 : 1;
+    const int splits = choose_splits(c, int(n), prec);
+    esp_status st = ensure_scratch(c, n, splits, host_io, n_walkers);
+    if (st != ESP_OK)
+        return st;
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    c->timed_valid = false;
+    if (c->timing && (e = cudaEventRecord(c->ev[0], s)) != cudaSuccess)
+        return cuda_fail(e, "recording a timing event");
+    const double *d_pos = positions;
+    if (host_io) {
+        if ((e = cudaMemcpyAsync(c->in.p, positions, size_t(n) * 3 * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "copying positions to the device");
+        d_pos = static_cast<const double *>(c->in.p);
+    }
+    Staged stg = staged_view(c, n);
+    if ((e = launch_stage(d_pos, int(n), c->opt.qm_center, stg, s)) != cudaSuccess)
+        return cuda_fail(e, "staging positions");
+    EvalArgs a;
+    a.n_pos = int(n);
+    a.n_splits = splits;
+    a.n_tiles = c->n_tiles;
+    a.tile_size = c->env.tile_size;
+    a.pos = stg;
+    a.tiles = static_cast<const TileMeta *>(c->tiles.p);
+    a.rec32 = static_cast<const float *>(c->rec32.p);
+    a.rec64 = static_cast<const double *>(c->rec64.p);
+    a.boys32 = static_cast<const float *>(c->boys32.p);
+    a.boys64 = static_cast<const double *>(c->boys64.p);
+    a.partial = static_cast<double *>(c->partial.p);
+    a.near_r = float(c->opt.near_radius < 0.0 ? 1.5 : c->opt.near_radius);
+    if (c->timing && (e = cudaEventRecord(c->ev[1], s)) != cudaSuccess)
+        return cuda_fail(e, "recording a timing event");
+    if (c->n_tiles == 0) {
+        if ((e = cudaMemsetAsync(a.partial, 0, size_t(n) * splits * sizeof(double), s)) != cudaSuccess)
+            return cuda_fail(e, "clearing partial sums");
+    } else if ((e = launch_potential(prec, a, c->threads[prec], c->ppt[prec], s)) != cudaSuccess) {
+        return cuda_fail(e, "launching the potential kernel");
+    }
+    if (c->timing && (e = cudaEventRecord(c->ev[2], s)) != cudaSuccess)
+        return cuda_fail(e, "recording a timing event");
+    double *dV = (!host_io && V_out) ? V_out : static_cast<double *>(c->vout.p);
+    if ((e = launch_reduce(a.partial, splits, int(n), dV, s)) != cudaSuccess)
+        return cuda_fail(e, "launching the partial-sum reduction");
+    double *dE = nullptr;
+    if (E_out) {
+        dE = host_io ? static_cast<double *>(c->eout.p) : E_out;
+        if ((e = launch_walkers(dV, int(n_walkers), int(n_elec), dE, s)) != cudaSuccess)
+            return cuda_fail(e, "launching the walker-energy reduction");
+    }
+    if (c->timing) {
+        if ((e = cudaEventRecord(c->ev[3], s)) != cudaSuccess)
+            return cuda_fail(e, "recording a timing event");
+        c->timed_valid = true;
+    }
+    if (host_io) {
+        if (V_out && (e = cudaMemcpyAsync(V_out, dV, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+                         cudaSuccess)
+            return cuda_fail(e, "copying potentials to the host");
+        if (E_out &&
+            (e = cudaMemcpyAsync(E_out, dE, size_t(n_walkers) * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+            return cuda_fail(e, "copying walker energies to the host");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "evaluation");
+    }
+    return ESP_OK;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf &b, const std::vector<T> &v, int64_t &bytes)
+{
+    size_t n = v.size() * sizeof(T);
+    cudaError_t e = b.ensure(std::max<size_t>(n, 16));
+    if (e != cudaSuccess)
+        return e;
+    bytes += int64_t(b.bytes);
+    if (n == 0)
+        return cudaSuccess;
+    return cudaMemcpy(b.p, v.data(), n, cudaMemcpyHostToDevice);
+}
+
+void release_all(esp_ctx *c)
+{
+    for (cudaEvent_t &ev : c->ev)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+    DevBuf *bufs[] = {&c->tiles, &c->rec32, &c->rec64, &c->boys32, &c->boys64,
+                      &c->in, &c->stage, &c->partial, &c->vout, &c->eout};
+    for (DevBuf *b : bufs)
+        b->release();
+}
+
+template <int L>
+double host_tile(const double *rec, int n, const double *C, const double *boys)
+{
+    constexpr int st = rec64_stride(L);
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double *r = rec + j * st;
+        double dx = r[0] - C[0], dy = r[1] - C[1], dz = r[2] - C[2];
+        double sp = r[3];
+        double F[L + 1];
+        if constexpr (L == 0) {
+            boys_eval<L, double>((sp * sp) * (dx * dx + dy * dy + dz * dz), boys, F);
+            acc += r[4] * F[0];
+        } else {
+            double x = sp * dx, y = sp * dy, z = sp * dz;
+            boys_eval<L, double>(x * x + y * y + z * z, boys, F);
+            acc += hermite_contract<L, double>(F, x, y, z, r + 4);
+        }
+    }
+    return acc;
+}
+
+} // namespace
+
+extern "C" {
+
+void esp_default_options(esp_options *opt)
+{
+    if (!opt)
+        return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->size = int32_t(sizeof(esp_options));
+    opt->precision = ESP_FP32C;
+    opt->screen_tol = 1e-12;
+    opt->cuda_stream = nullptr;
+    opt->device = -1;
+    opt->near_radius = -1.0;
+}
+
+int32_t esp_abi_version(void) { return ESP_ABI_VERSION; }
+
+const char *esp_last_error(void) { return g_last_error.c_str(); }
+
+const char *esp_status_string(esp_status s)
+{
+    switch (s) {
+    case ESP_OK: return "ok";
+    case ESP_ERR_INVALID: return "invalid argument";
+    case ESP_ERR_OOM: return "out of memory";
+    case ESP_ERR_CUDA: return "CUDA error";
+    case ESP_ERR_TIMEOUT: return "device wait timed out";
+    case ESP_ERR_STATE: return "context busy or invalid";
+    case ESP_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const esp_gauss_pair *pairs,
+                      const double *weights, int64_t n_pairs, const esp_options *opt_in, esp_ctx **out)
+{
+    g_last_error.clear();
+    if (!out)
+        return fail(ESP_ERR_INVALID, "out is NULL");
+    esp_options opt;
+    esp_default_options(&opt);
+    if (opt_in) {
+        if (opt_in->size != int32_t(sizeof(esp_options)))
+            return fail(ESP_ERR_INVALID, "esp_options.size is %d, expected %d (call esp_default_options)",
+                        opt_in->size, int(sizeof(esp_options)));
+        opt = *opt_in;
+    }
+    if (opt.precision != ESP_FP64 && opt.precision != ESP_FP32C)
+        return fail(ESP_ERR_INVALID, "unknown precision %d", opt.precision);
+    if (opt.flags & ~ESP_FLAG_HOST_ONLY)
+        return fail(ESP_ERR_INVALID, "unknown flags 0x%x", opt.flags);
+    if (!(opt.near_radius < 1e6))
+        return fail(ESP_ERR_INVALID, "bad near_radius");
+    const int thr_ok[] = {0, 64, 128, 256};
+    bool tok = false;
+    for (int t : thr_ok)
+        tok |= opt.threads_per_block == t;
+    if (!tok || opt.positions_per_thread < 0 || opt.positions_per_thread > 4 || opt.pair_splits < 0)
+        return fail(ESP_ERR_INVALID, "bad launch-shape options");
+
+    esp_ctx *c = new (std::nothrow) esp_ctx();
+    if (!c)
+        return fail(ESP_ERR_OOM, "host allocation of the context");
+    c->opt = opt;
+    std::string err;
+    esp_status st = build_environment(charges, n_charges, pairs, weights, n_pairs, opt, c->env, err);
+    if (st != ESP_OK) {
+        delete c;
+        return fail(st, "%s", err.c_str());
+    }
+    c->n_tiles = int(c->env.tiles.size());
+    if (opt.flags & ESP_FLAG_HOST_ONLY) {
+        c->device = -1;
+        *out = c;
+        return ESP_OK;
+    }
+    int dev = opt.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        delete c;
+        return fail(ESP_ERR_CUDA, "no CUDA device");
+    }
+    c->device = dev;
+    DeviceGuard dg(dev);
+    if (!dg.ok) {
+        delete c;
+        return fail(ESP_ERR_CUDA, "cannot select device %d", dev);
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
+    c->n_tiles = int(c->env.tiles.size());
+    if (opt.threads_per_block) {
+        c->threads[0] = c->threads[1] = opt.threads_per_block;
+    }
+    if (opt.positions_per_thread) {
+        c->ppt[0] = c->ppt[1] = opt.positions_per_thread;
+    }
+    cudaError_t e;
+    int64_t bytes = 0;
+    if ((e = upload(c->tiles, c->env.tiles, bytes)) != cudaSuccess ||
+        (e = upload(c->rec32, c->env.rec32, bytes)) != cudaSuccess ||
+        (e = upload(c->rec64, c->env.rec64, bytes)) != cudaSuccess ||
+        (e = upload(c->boys32, boys_table32(), bytes)) != cudaSuccess ||
+        (e = upload(c->boys64, boys_table64(), bytes)) != cudaSuccess) {
+        release_all(c);
+        delete c;
+        return cuda_fail(e, "uploading the environment");
+    }
+    c->device_bytes = bytes;
+    // keep a host copy of the records only while it is small (test hook use)
+    if (c->env.rec64.size() * sizeof(double) > (size_t(256) << 20)) {
+        c->host_copy = false;
+        std::vector<float>().swap(c->env.rec32);
+        std::vector<double>().swap(c->env.rec64);
+    }
+    *out = c;
+    return ESP_OK;
+}
+
+esp_status esp_eval(esp_ctx *ctx, const double *positions, int64_t n, double *V_out)
+{
+    g_last_error.clear();
+    if (!valid_ctx(ctx) || ctx->device < 0)
+        return fail(ESP_ERR_STATE, "invalid or host-only context");
+    if (n > 0 && !V_out)
+        return fail(ESP_ERR_INVALID, "V_out is NULL");
+    return run_eval(ctx, positions, n, V_out, 0, 0, nullptr);
+}
+
+esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_walkers, int64_t n_elec,
+                            double *V_out, double *E_out)
+{
+    g_last_error.clear();
+    if (!valid_ctx(ctx) || ctx->device < 0)
+        return fail(ESP_ERR_STATE, "invalid or host-only context");
+    if (n_walkers < 0 || n_elec < 0 || n_walkers > (int64_t(1) << 30) || n_elec > (int64_t(1) << 20))
+        return fail(ESP_ERR_INVALID, "bad walker counts");
+    if (n_walkers * n_elec > (int64_t(1) << 30))
+        return fail(ESP_ERR_INVALID, "too many positions");
+    if (n_walkers > 0 && !E_out)
+        return fail(ESP_ERR_INVALID, "E_out is NULL");
+    if (n_walkers > 0 && n_elec == 0) {
+        // every walker has zero electrons: its energy is 0
+        DeviceGuard dg(ctx->device);
+        Space se = classify(E_out, ctx->device);
+        if (se == Space::Invalid)
+            return fail(ESP_ERR_INVALID, "E_out on another device");
+        if (se == Space::Host) {
+            std::memset(E_out, 0, size_t(n_walkers) * sizeof(double));
+            return ESP_OK;
+        }
+        cudaError_t e = cudaMemsetAsync(E_out, 0, size_t(n_walkers) * sizeof(double), ctx->stream);
+        return e == cudaSuccess ? ESP_OK : cuda_fail(e, "clearing walker energies");
+    }
+    return run_eval(ctx, positions, n_walkers * n_elec, V_out, n_walkers, n_elec, E_out);
+}
+
+esp_status esp_set_precision(esp_ctx *ctx, int32_t precision)
+{
+    if (!valid_ctx(ctx))
+        return fail(ESP_ERR_STATE, "invalid context");
+    if (precision != ESP_FP64 && precision != ESP_FP32C)
+        return fail(ESP_ERR_INVALID, "unknown precision %d", precision);
+    BusyGuard busy(ctx->busy);
+    if (!busy.acquired)
+        return fail(ESP_ERR_STATE, "context is in use by another thread");
+    ctx->opt.precision = precision;
+    return ESP_OK;
+}
+
+esp_status esp_get_info(const esp_ctx *ctx, esp_info *info)
+{
+    if (!valid_ctx(ctx) || !info)
+        return fail(ESP_ERR_INVALID, "invalid context or info pointer");
+    std::memset(info, 0, sizeof(*info));
+    info->n_point_charges = ctx->env.n_point_charges;
+    info->n_pairs_in = ctx->env.n_pairs_in;
+    info->n_distributions = ctx->env.n_distributions;
+    info->n_screened = ctx->env.n_screened;
+    for (int l = 0; l <= kMaxL; ++l)
+        info->n_by_L[l] = ctx->env.n_by_L[l];
+    info->n_tiles = ctx->n_tiles;
+    info->device_bytes = ctx->device_bytes;
+    info->precision = ctx->opt.precision;
+    info->tile_size = ctx->env.tile_size;
+    int p = ctx->opt.precision == ESP_FP64 ? 0 : 1;
+    info->threads_per_block = ctx->threads[p];
+    info->positions_per_thread = ctx->ppt[p];
+    info->pair_splits = ctx->opt.pair_splits;
+    info->device = ctx->device;
+    return ESP_OK;
+}
+
+esp_status esp_set_timing(esp_ctx *ctx, int32_t enable)
+{
+    if (!valid_ctx(ctx) || ctx->device < 0)
+        return fail(ESP_ERR_STATE, "invalid or host-only context");
+    BusyGuard busy(ctx->busy);
+    if (!busy.acquired)
+        return fail(ESP_ERR_STATE, "context is in use by another thread");
+    DeviceGuard dg(ctx->device);
+    if (enable && !ctx->ev[0]) {
+        for (cudaEvent_t &ev : ctx->ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "creating timing events");
+        }
+    }
+    ctx->timing = enable != 0;
+    ctx->timed_valid = false;
+    return ESP_OK;
+}
+
+esp_status esp_last_timing(esp_ctx *ctx, double *potential_ms, double *pipeline_ms)
+{
+    if (!valid_ctx(ctx) || ctx->device < 0)
+        return fail(ESP_ERR_STATE, "invalid or host-only context");
+    if (!ctx->timing || !ctx->timed_valid)
+        return fail(ESP_ERR_STATE, "no timed evaluation (call esp_set_timing first)");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "waiting for the timed evaluation");
+    float k = 0.f, t = 0.f;
+    if ((e = cudaEventElapsedTime(&k, ctx->ev[1], ctx->ev[2])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[3])) != cudaSuccess)
+        return cuda_fail(e, "reading timing events");
+    if (potential_ms)
+        *potential_ms = k;
+    if (pipeline_ms)
+        *pipeline_ms = t;
+    return ESP_OK;
+}
+
+esp_status esp_synchronize(esp_ctx *ctx)
+{
+    if (!valid_ctx(ctx) || ctx->device < 0)
+        return fail(ESP_ERR_STATE, "invalid or host-only context");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? ESP_OK : cuda_fail(e, "synchronize");
+}
+
+void esp_destroy(esp_ctx *ctx)
+{
+    if (!valid_ctx(ctx))
+        return;
+    if (ctx->device >= 0) {
+        DeviceGuard dg(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        release_all(ctx);
+    }
+    ctx->magic = 0;
+    delete ctx;
+}
+
+esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_out)
+{
+    if (!F_out || nmax < 0 || nmax > kMaxL || !(T >= 0.0) || !(T < 1e30))
+        return fail(ESP_ERR_INVALID, "bad Boys arguments");
+    if (precision == ESP_FP64) {
+        const double *tab = boys_table64().data();
+        double F[kMaxL + 1];
+        switch (nmax) {
+        case 0: { double G[1]; boys_eval<0, double>(T, tab, G); F[0] = G[0]; break; }
+        case 1: { double G[2]; boys_eval<1, double>(T, tab, G); for (int i = 0; i < 2; ++i) F[i] = G[i]; break; }
+        case 2: { double G[3]; boys_eval<2, double>(T, tab, G); for (int i = 0; i < 3; ++i) F[i] = G[i]; break; }
+        case 3: { double G[4]; boys_eval<3, double>(T, tab, G); for (int i = 0; i < 4; ++i) F[i] = G[i]; break; }
+        default: { double G[5]; boys_eval<4, double>(T, tab, G); for (int i = 0; i < 5; ++i) F[i] = G[i]; break; }
+        }
+        for (int i = 0; i <= nmax; ++i)
+            F_out[i] = F[i];
+        return ESP_OK;
+    }
+    if (precision == ESP_FP32C) {
+        const float *tab = boys_table32().data();
+        float F[kMaxL + 1];
+        float Tf = float(T);
+        switch (nmax) {
+        case 0: { float G[1]; boys_eval<0, float>(Tf, tab, G); F[0] = G[0]; break; }
+        case 1: { float G[2]; boys_eval<1, float>(Tf, tab, G); for (int i = 0; i < 2; ++i) F[i] = G[i]; break; }
+        case 2: { float G[3]; boys_eval<2, float>(Tf, tab, G); for (int i = 0; i < 3; ++i) F[i] = G[i]; break; }
+        case 3: { float G[4]; boys_eval<3, float>(Tf, tab, G); for (int i = 0; i < 4; ++i) F[i] = G[i]; break; }
+        default: { float G[5]; boys_eval<4, float>(Tf, tab, G); for (int i = 0; i < 5; ++i) F[i] = G[i]; break; }
+        }
+        for (int i = 0; i <= nmax; ++i)
+            F_out[i] = F[i];
+        return ESP_OK;
+    }
+    return fail(ESP_ERR_INVALID, "unknown precision");
+}
+
+esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int64_t n, double *V_out)
+{
+    if (!valid_ctx(ctx) || n < 0 || (n > 0 && (!positions || !V_out)))
+        return fail(ESP_ERR_INVALID, "bad arguments");
+    if (!ctx->host_copy)
+        return fail(ESP_ERR_UNSUPPORTED, "host copy of the records was dropped (environment too large)");
+    const double *boys = boys_table64().data();
+    const double *rec = ctx->env.rec64.data();
+    for (int64_t i = 0; i < n; ++i) {
+        double C[3];
+        for (int d = 0; d < 3; ++d)
+            C[d] = positions[3 * i + d] - ctx->opt.qm_center[d];
+        double s = 0.0, cc = 0.0;
+        for (const TileMeta &m : ctx->env.tiles) {
+            const double *r = rec + m.off64;
+            double v = 0.0;
+            switch (m.cls) {
+            case 0: v = host_tile<0>(r, m.n, C, boys); break;
+            case 1: v = host_tile<1>(r, m.n, C, boys); break;
+            case 2: v = host_tile<2>(r, m.n, C, boys); break;
+            case 3: v = host_tile<3>(r, m.n, C, boys); break;
+            case 4: v = host_tile<4>(r, m.n, C, boys); break;
+            default:
+                for (int j = 0; j < m.n; ++j) {
+                    double dx = r[4 * j] - C[0], dy = r[4 * j + 1] - C[1], dz = r[4 * j + 2] - C[2];
+                    v += r[4 * j + 3] / std::sqrt(dx * dx + dy * dy + dz * dz);
+                }
+            }
+            double t = s + v, bp = t - s;
+            cc += (s - (t - bp)) + (v - bp);
+            s = t;
+        }
+        V_out[i] = s + cc;
+    }
+    return ESP_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,208 @@
+// Internal definitions shared by the pair builder (host) and the kernels.
+//
+// A Hermite distribution is the Gaussian product chi_a chi_b of one shell pair
+// written in McMurchie-Davidson form (Helgaker, Joergensen & Olsen, Sec. 9.5):
+//   chi_a chi_b = sum_{t+u+v<=L} D_tuv  d^t/dPx^t d^u/dPy^u d^v/dPz^v exp(-p|r-P|^2)
+// and its potential at C is (2 pi / p) sum D_tuv R_tuv(p, P - C) with
+//   R^n_000 = (-2p)^n F_n(p|P-C|^2),
+//   R^n_{t+1,u,v} = t R^{n+1}_{t-1,u,v} + X_PC R^{n+1}_{t,u,v}  (same in u, v).
+// Substituting R^n_tuv = p^{n+(t+u+v)/2} S^n_tuv removes p from the recursion:
+//   S^n_000 = (-2)^n F_n(T),  S^n_{t+1,u,v} = t S^{n+1}_{t-1,u,v} + x S^{n+1}_{t,u,v},
+// with scaled coordinates x = sqrt(p) (P - C) and T = |x|^2.  The builder
+// therefore stores G_tuv = (2 pi / p) p^{(t+u+v)/2} D_tuv, and a distribution's
+// potential is sum_tuv G_tuv S^0_tuv.  This is the generalisation of one cell
+// term rho(r_m)/|r_new - r_m| of Eq. ElectrostaticField: an s distribution
+// with p -> infinity gives G_000 F_0 -> q / |P - C|.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define ESP_HD __host__ __device__ __forceinline__
+#else
+#define ESP_HD inline
+#endif
+
+namespace esp {
+
+constexpr int kMaxL = 4;
+constexpr int kClassPoint = 5;          // tile class of point charges
+ESP_HD constexpr int num_hermite(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+
+// FP32 record stride (floats): [Px, Py, Pz, p or sqrt(p), G_0 .. G_{n-1}], padded to 4.
+ESP_HD constexpr int rec32_stride(int L) { return L == 0 ? 8 : ((4 + (L == 1 ? 4 : L == 2 ? 10 : L == 3 ? 20 : 35) + 3) / 4) * 4; }
+// FP64 record stride (doubles): [Px, Py, Pz, sqrt(p), G_0 .. G_{n-1}], padded to 2.
+ESP_HD constexpr int rec64_stride(int L) { return ((4 + (L == 0 ? 1 : L == 1 ? 4 : L == 2 ? 10 : L == 3 ? 20 : 35) + 1) / 2) * 2; }
+constexpr int kPointStride64 = 4;        // [x, y, z, Z]
+
+// Boys tables: rows at T_i = i / 8 (exact in binary), each row F_0 .. F_{nmax}
+// followed by exp(-T_i).
+constexpr float kBoysStep = 0.125f;
+constexpr float kBoysInvStep = 8.0f;
+constexpr int kBoys32Terms = 6;          // Taylor terms (k = 0..5) of the FP32 table
+constexpr float kBoys32Tmax = 30.0f;     // asymptotic form at and above this T
+constexpr int kBoys32Rows = 241;         // T_i up to 30
+constexpr int kBoys32Row = 12;           // F_0..F_9, exp(-T_i), pad
+constexpr int kBoys64Terms = 9;          // Taylor terms (k = 0..8) of the FP64 table
+constexpr double kBoys64Tmax = 45.0;
+constexpr int kBoys64Rows = 361;         // T_i up to 45
+constexpr int kBoys64Row = 16;           // F_0..F_12, exp(-T_i), pad x2
+
+struct TileMeta {
+    int32_t cls;      // 0..4 = L of every distribution in the tile, 5 = point charges
+    int32_t n;        // entries in the tile
+    int32_t off32;    // float offset of the first FP32 record (distributions only)
+    int32_t off64;    // double offset of the first FP64 record
+    float cx, cy, cz; // bounding-sphere centre (recentred coordinates)
+    float rad;        // bounding-sphere radius
+    float pmin;       // smallest exponent p in the tile (0 for point tiles)
+    float qabs;       // sum of absolute charge bounds of the tile's entries
+    float pad0, pad1;
+};
+static_assert(sizeof(TileMeta) == 48, "TileMeta layout");
+
+// Canonical order of Hermite indices: by N = t+u+v, then t descending, then u descending.
+ESP_HD constexpr int hidx(int t, int u, int v)
+{
+    int N = t + u + v;
+    int base = N * (N + 1) * (N + 2) / 6;
+    int off = 0;
+    for (int tt = N; tt > t; --tt)
+        off += N - tt + 1;
+    return base + off + (N - t - u);
+}
+
+// ---------------------------------------------------------------------------
+// Boys function from a Taylor table + downward recursion (T < Tmax) or the
+// asymptotic series with upward recursion (T >= Tmax).  Templated on the real
+// type so the FP32 and FP64 kernels (and host test hooks) share one definition.
+//   F_n(T_i + d) = sum_k F_{n+k}(T_i) (-d)^k / k!            (Taylor in T)
+//   F_n = (2 T F_{n+1} + e^{-T}) / (2n+1)                    (downward)
+//   F_0 ~ sqrt(pi) / (2 sqrt(T)),  F_{n+1} ~ (2n+1)/(2T) F_n  (asymptotic)
+// ---------------------------------------------------------------------------
+template <typename R> struct BoysConst;
+template <> struct BoysConst<float> {
+    static constexpr int kTerms = kBoys32Terms;
+    static constexpr int kRow = kBoys32Row;
+    static constexpr int kExpCol = 10;
+    ESP_HD static float tmax() { return kBoys32Tmax; }
+};
+template <> struct BoysConst<double> {
+    static constexpr int kTerms = kBoys64Terms;
+    static constexpr int kRow = kBoys64Row;
+    static constexpr int kExpCol = 13;
+    ESP_HD static double tmax() { return kBoys64Tmax; }
+};
+
+ESP_HD float esp_rsqrt(float x)
+{
+#if defined(__CUDA_ARCH__)
+    float y = rsqrtf(x);
+#else
+    float y = 1.0f / sqrtf(x);
+#endif
+    // one Newton step makes the error symmetric about zero (no bias across terms)
+    float h = x * y;
+    float e = fmaf(-h, y, 1.0f);
+    return fmaf(0.5f * e, y, y);
+}
+ESP_HD double esp_rsqrt(double x)
+{
+#if defined(__CUDA_ARCH__)
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
+template <int L, typename R>
+ESP_HD void boys_eval(R T, const R *__restrict__ tab, R (&F)[L + 1])
+{
+    using C = BoysConst<R>;
+    if (T >= C::tmax()) {
+        R rs = esp_rsqrt(T);
+        F[0] = R(0.88622692545275801365) * rs; // sqrt(pi)/2
+        R h = R(0.5) * rs * rs;                // 1/(2T)
+#pragma unroll
+        for (int n = 1; n <= L; ++n)
+            F[n] = F[n - 1] * (R(2 * n - 1) * h);
+    } else {
+        int i = (int)(T * R(8) + R(0.5));
+        R d = T - R(i) * R(0.125);             // exact: T and T_i are within 1/16
+        const R *row = tab + i * C::kRow;
+        R md = -d;
+        R f = row[L + C::kTerms - 1];
+#pragma unroll
+        for (int k = C::kTerms - 2; k >= 0; --k)
+            f = f * (md * R(1.0 / (k + 1))) + row[L + k];
+        F[L] = f;
+        if constexpr (L > 0) {
+            // exp(-T) = exp(-T_i) * exp(-d), exp(-d) by its Taylor series (|d| <= 1/16)
+            R e = R(1);
+#pragma unroll
+            for (int k = C::kTerms; k >= 1; --k)
+                e = e * (md * R(1.0 / k)) + R(1);
+            e *= row[C::kExpCol];
+            R T2 = T + T;
+#pragma unroll
+            for (int n = L - 1; n >= 0; --n)
+                F[n] = (T2 * F[n + 1] + e) * R(1.0 / (2 * n + 1));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sum_tuv G_tuv S^0_tuv for one distribution of total angular momentum L at
+// scaled offset (x, y, z) = sqrt(p) (P - C), given F_0..F_L(T).
+// ---------------------------------------------------------------------------
+template <int L, typename R>
+ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const R *__restrict__ G)
+{
+    if constexpr (L == 0) {
+        return G[0] * F[0];
+    } else {
+    // S[n][h] for levels n = 0..L; level n needs N <= L - n
+    R S[L + 1][35];
+#pragma unroll
+    for (int n = L; n >= 0; --n) {
+        R s0 = F[n];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+            s0 = -R(2) * s0;
+        S[n][0] = s0;
+#pragma unroll
+        for (int N = 1; N <= L - n; ++N) {
+#pragma unroll
+            for (int t = N; t >= 0; --t) {
+#pragma unroll
+                for (int u = N - t; u >= 0; --u) {
+                    const int v = N - t - u;
+                    R val;
+                    if (t > 0) {
+                        val = x * S[n + 1][hidx(t - 1, u, v)];
+                        if (t > 1)
+                            val += R(t - 1) * S[n + 1][hidx(t - 2, u, v)];
+                    } else if (u > 0) {
+                        val = y * S[n + 1][hidx(t, u - 1, v)];
+                        if (u > 1)
+                            val += R(u - 1) * S[n + 1][hidx(t, u - 2, v)];
+                    } else {
+                        val = z * S[n + 1][hidx(t, u, v - 1)];
+                        if (v > 1)
+                            val += R(v - 1) * S[n + 1][hidx(t, u, v - 2)];
+                    }
+                    S[n][hidx(t, u, v)] = val;
+                }
+            }
+        }
+    }
+    R acc = G[0] * S[0][0];
+#pragma unroll
+    for (int h = 1; h < num_hermite(L); ++h)
+        acc += G[h] * S[0][h];
+    return acc;
+    }
+}
+
+} // namespace esp

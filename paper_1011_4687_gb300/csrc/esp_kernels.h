@@ -1,0 +1,41 @@
+// Device-side launch interface of the potential kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "esp_internal.h"
+
+namespace esp {
+
+// Recentred positions, structure of arrays: FP64 copy and FP32 hi + lo split
+// (hi = fp32(x), lo = fp32(x - hi)), so FP32 code can form P - C without
+// losing the low bits of C.
+struct Staged {
+    double *x64, *y64, *z64;
+    float *xh, *yh, *zh, *xl, *yl, *zl;
+};
+
+struct EvalArgs {
+    int n_pos;
+    int n_splits;     // tiles are dealt round-robin to this many splits
+    int n_tiles;
+    int tile_size;
+    Staged pos;
+    const TileMeta *tiles;
+    const float *rec32;
+    const double *rec64;
+    const float *boys32;
+    const double *boys64;
+    double *partial;  // [n_splits][n_pos], FP64
+    float near_r;     // FP32C: FP64 re-evaluation radius around a tile's bounding sphere
+};
+
+cudaError_t launch_stage(const double *pos_in, int n, const double center[3], const Staged &st,
+                         cudaStream_t s);
+// precision: 0 = FP64, 1 = FP32C.  threads in {64, 128, 256}, ppt in {1, 2, 4}.
+cudaError_t launch_potential(int precision, const EvalArgs &a, int threads, int ppt, cudaStream_t s);
+size_t potential_smem_bytes(int precision, int tile_size);
+cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s);
+cudaError_t launch_walkers(const double *V, int n_walkers, int n_elec, double *E, cudaStream_t s);
+
+} // namespace esp

@@ -1,0 +1,279 @@
+"""ctypes binding of libesp_gb300.so (include/esp.h).
+
+Argument marshalling only: every step of an evaluation runs in the library's
+CUDA kernels.  There is no CPU fallback; if the compiled library is missing
+the import of this module's functions raises.
+
+Positions and outputs may be numpy arrays (host; the call is synchronous) or
+torch CUDA tensors (device; the call is enqueued on the context's stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build_lib
+
+ESP_OK, ESP_ERR_INVALID, ESP_ERR_OOM, ESP_ERR_CUDA, ESP_ERR_TIMEOUT, ESP_ERR_STATE, ESP_ERR_UNSUPPORTED = range(7)
+FP64, FP32C = 0, 1
+PRECISIONS = {"fp64": FP64, "fp32c": FP32C}
+
+GAUSS_PAIR_DTYPE = np.dtype([("A", "<f8", (3,)), ("alpha", "<f8"), ("lmn_a", "<i4", (3,)), ("pad_a", "<i4"),
+                             ("B", "<f8", (3,)), ("beta", "<f8"), ("lmn_b", "<i4", (3,)), ("pad_b", "<i4")])
+POINT_CHARGE_DTYPE = np.dtype([("xyz", "<f8", (3,)), ("Z", "<f8")])
+assert GAUSS_PAIR_DTYPE.itemsize == 96 and POINT_CHARGE_DTYPE.itemsize == 32
+
+
+class EspError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("esp status %d: %s" % (status, message))
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_int32), ("precision", ctypes.c_int32), ("screen_tol", ctypes.c_double),
+                ("qm_center", ctypes.c_double * 3), ("cuda_stream", ctypes.c_void_p),
+                ("device", ctypes.c_int32), ("tile_size", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("positions_per_thread", ctypes.c_int32),
+                ("pair_splits", ctypes.c_int32), ("flags", ctypes.c_int32), ("near_radius", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_point_charges", ctypes.c_int64), ("n_pairs_in", ctypes.c_int64),
+                ("n_distributions", ctypes.c_int64), ("n_screened", ctypes.c_int64),
+                ("n_by_L", ctypes.c_int64 * 5), ("n_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("tile_size", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("positions_per_thread", ctypes.c_int32),
+                ("pair_splits", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["n_by_L"] = list(self.n_by_L)
+        return d
+
+
+EXPORTED = ["esp_default_options", "esp_create", "esp_eval", "esp_eval_walkers", "esp_set_precision",
+            "esp_get_info", "esp_synchronize", "esp_destroy", "esp_status_string", "esp_last_error",
+            "esp_abi_version", "esp_debug_boys", "esp_debug_host_eval", "esp_set_timing", "esp_last_timing"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return build_lib.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the compiled library (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build_lib.LIB
+    if build_if_missing and build_lib.is_stale():
+        build_lib.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libesp_gb300.so is not built (run paper_1011_4687_gb300.build_lib); "
+                           "there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.esp_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.esp_default_options.restype = None
+    lib.esp_create.argtypes = [P, i64, P, P, i64, ctypes.POINTER(Options), ctypes.POINTER(P)]
+    lib.esp_create.restype = ctypes.c_int
+    lib.esp_eval.argtypes = [P, P, i64, P]
+    lib.esp_eval.restype = ctypes.c_int
+    lib.esp_eval_walkers.argtypes = [P, P, i64, i64, P, P]
+    lib.esp_eval_walkers.restype = ctypes.c_int
+    lib.esp_set_precision.argtypes = [P, i32]
+    lib.esp_set_precision.restype = ctypes.c_int
+    lib.esp_get_info.argtypes = [P, ctypes.POINTER(Info)]
+    lib.esp_get_info.restype = ctypes.c_int
+    lib.esp_synchronize.argtypes = [P]
+    lib.esp_synchronize.restype = ctypes.c_int
+    lib.esp_destroy.argtypes = [P]
+    lib.esp_destroy.restype = None
+    lib.esp_status_string.argtypes = [ctypes.c_int]
+    lib.esp_status_string.restype = ctypes.c_char_p
+    lib.esp_last_error.argtypes = []
+    lib.esp_last_error.restype = ctypes.c_char_p
+    lib.esp_abi_version.restype = i32
+    lib.esp_debug_boys.argtypes = [i32, i32, d, P]
+    lib.esp_debug_boys.restype = ctypes.c_int
+    lib.esp_debug_host_eval.argtypes = [P, P, i64, P]
+    lib.esp_debug_host_eval.restype = ctypes.c_int
+    lib.esp_set_timing.argtypes = [P, i32]
+    lib.esp_set_timing.restype = ctypes.c_int
+    lib.esp_last_timing.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.esp_last_timing.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != ESP_OK:
+        msg = _lib.esp_last_error().decode(errors="replace")
+        raise EspError(status, msg or _lib.esp_status_string(status).decode())
+
+
+def default_options() -> Options:
+    o = Options()
+    load().esp_default_options(ctypes.byref(o))
+    return o
+
+
+def pack_pairs(pairs) -> np.ndarray:
+    """PairList (SoA) -> array of esp_gauss_pair."""
+    n = len(pairs)
+    a = np.zeros(n, GAUSS_PAIR_DTYPE)
+    if n:
+        a["A"], a["alpha"], a["lmn_a"] = pairs.A, pairs.alpha, pairs.la
+        a["B"], a["beta"], a["lmn_b"] = pairs.B, pairs.beta, pairs.lb
+    return a
+
+
+def pack_charges(xyz, Z) -> np.ndarray:
+    xyz = np.asarray(xyz, np.float64).reshape(-1, 3)
+    a = np.zeros(xyz.shape[0], POINT_CHARGE_DTYPE)
+    if xyz.shape[0]:
+        a["xyz"], a["Z"] = xyz, np.asarray(Z, np.float64).reshape(-1)
+    return a
+
+
+def _ptr(x):
+    """(pointer, is_device) of a numpy array or torch tensor."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous or x.dtype != np.float64:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return ctypes.c_void_p(x.ctypes.data), False
+    import torch  # noqa: F401  (only for device tensors)
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    return ctypes.c_void_p(x.data_ptr()), bool(x.is_cuda)
+
+
+class Environment:
+    """A built environment on one device (owns an esp_ctx)."""
+
+    def __init__(self, nuclei_xyz, nuclei_Z, pairs, precision="fp32c", screen_tol=1e-12,
+                 qm_center=(0.0, 0.0, 0.0), stream=None, device=-1, tile_size=0, threads_per_block=0,
+                 positions_per_thread=0, pair_splits=0, near_radius=-1.0):
+        lib = load()
+        opt = default_options()
+        opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opt.screen_tol = float(screen_tol)
+        opt.qm_center[:] = [float(v) for v in qm_center]
+        opt.cuda_stream = ctypes.c_void_p(int(stream) if stream is not None else 0)
+        opt.device = int(device)
+        opt.tile_size = int(tile_size)
+        opt.threads_per_block = int(threads_per_block)
+        opt.positions_per_thread = int(positions_per_thread)
+        opt.pair_splits = int(pair_splits)
+        opt.near_radius = float(near_radius)
+        ch = pack_charges(nuclei_xyz, nuclei_Z)
+        pr = pack_pairs(pairs)
+        w = np.ascontiguousarray(pairs.w, np.float64)
+        ctx = ctypes.c_void_p()
+        _check(lib.esp_create(ch.ctypes.data if ch.size else None, ch.size,
+                              pr.ctypes.data if pr.size else None, w.ctypes.data if w.size else None,
+                              pr.size, ctypes.byref(opt), ctypes.byref(ctx)))
+        self._ctx = ctx
+        self.stream = stream
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            load().esp_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ---------------------------------------------------------------
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._ctx
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().esp_get_info(self._ctx, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def set_precision(self, precision):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(load().esp_set_precision(self._ctx, p))
+
+    def set_timing(self, enable: bool = True):
+        _check(load().esp_set_timing(self._ctx, int(bool(enable))))
+
+    def last_timing(self):
+        """(potential-kernel ms, device-pipeline ms) of the last evaluation."""
+        k, t = ctypes.c_double(), ctypes.c_double()
+        _check(load().esp_last_timing(self._ctx, ctypes.byref(k), ctypes.byref(t)))
+        return k.value, t.value
+
+    def synchronize(self):
+        _check(load().esp_synchronize(self._ctx))
+
+    def eval(self, positions, out=None):
+        """V at each position.  numpy in -> numpy out; CUDA tensor in -> CUDA tensor out."""
+        n = int(positions.shape[0]) if positions.ndim == 2 else int(positions.size // 3)
+        if out is None:
+            if isinstance(positions, np.ndarray):
+                out = np.zeros(n, np.float64)
+            else:
+                import torch
+                out = torch.empty(n, dtype=torch.float64, device=positions.device)
+        pp, _ = _ptr(positions)
+        po, _ = _ptr(out)
+        _check(load().esp_eval(self._ctx, pp, n, po))
+        return out
+
+    def eval_walkers(self, positions, n_walkers, n_elec, V_out=None, E_out=None, want_V=True):
+        """(V, E) with E[w] = -sum_e V[w, e]."""
+        host = isinstance(positions, np.ndarray)
+        if E_out is None:
+            if host:
+                E_out = np.zeros(n_walkers, np.float64)
+            else:
+                import torch
+                E_out = torch.empty(n_walkers, dtype=torch.float64, device=positions.device)
+        if V_out is None and want_V:
+            if host:
+                V_out = np.zeros(n_walkers * n_elec, np.float64)
+            else:
+                import torch
+                V_out = torch.empty(n_walkers * n_elec, dtype=torch.float64, device=positions.device)
+        pp, _ = _ptr(positions)
+        pv, _ = _ptr(V_out)
+        pe, _ = _ptr(E_out)
+        _check(load().esp_eval_walkers(self._ctx, pp, int(n_walkers), int(n_elec), pv, pe))
+        return V_out, E_out
+
+    def debug_host_eval(self, positions: np.ndarray) -> np.ndarray:
+        """Test hook: evaluate the built tiles on the host in FP64 (never used by eval)."""
+        pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+        V = np.zeros(pos.shape[0])
+        _check(load().esp_debug_host_eval(self._ctx, pos.ctypes.data, pos.shape[0], V.ctypes.data))
+        return V
+
+
+def debug_boys(precision, nmax: int, T: float) -> np.ndarray:
+    """Test hook: the device Boys algorithm of `precision`, run on the host."""
+    F = np.zeros(nmax + 1)
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(load().esp_debug_boys(p, int(nmax), float(T), F.ctypes.data))
+    return F
