@@ -198,9 +198,11 @@ int32_t esp_abi_version(void);
 esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_out);
 
 /* Test hook, not part of the evaluation path: evaluate a built context's
- * tiles on the host in FP64 with the device's Hermite code, so CPU tests can
- * check folding, screening and tiling of the pair builder.  positions and
- * V_out are host arrays.  esp_eval never calls this. */
+ * tiles on the host with the kernels' own per-tile code, in the context's
+ * precision (ESP_FP64: FP64; ESP_FP32C: the FP32-compensated arithmetic of
+ * the kernel, emulated in IEEE single precision), so CPU tests can check the
+ * pair builder and the error budget of the FP32 path without a GPU.
+ * positions and V_out are host arrays.  esp_eval never calls this. */
 esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int64_t n,
                                double *V_out);
 

@@ -50,6 +50,8 @@ def _load():
             lib.oracle_pair_potential.restype = d
             lib.oracle_potential.argtypes = [P, P, i64, P, P, P, P, P, P, P, i64, P, i64, P, ctypes.c_int]
             lib.oracle_potential.restype = ctypes.c_int
+            lib.oracle_abs_terms.argtypes = lib.oracle_potential.argtypes
+            lib.oracle_abs_terms.restype = ctypes.c_int
             lib.oracle_walker_energies.argtypes = [P, i64, i64, P]
             lib.oracle_walker_energies.restype = ctypes.c_int
             lib.oracle_max_threads.restype = ctypes.c_int
@@ -96,6 +98,23 @@ def potential(nuclei_xyz, nuclei_Z, pairs, positions, threads: int = 0) -> np.nd
     if rc != 0:
         raise ValueError("oracle rejected its input")
     return V
+
+
+def abs_terms(nuclei_xyz, nuclei_Z, pairs, positions, threads: int = 0) -> np.ndarray:
+    """K[N] = sum of |term| over every point charge and pair: the condition of V[N]."""
+    nx = _c(nuclei_xyz, np.float64).reshape(-1, 3)
+    nz = _c(nuclei_Z, np.float64).reshape(-1)
+    pos = _c(positions, np.float64).reshape(-1, 3)
+    A, al, la = _c(pairs.A, np.float64), _c(pairs.alpha, np.float64), _c(pairs.la, np.int32)
+    B, be, lb = _c(pairs.B, np.float64), _c(pairs.beta, np.float64), _c(pairs.lb, np.int32)
+    w = _c(pairs.w, np.float64)
+    K = np.zeros(pos.shape[0])
+    rc = _load().oracle_abs_terms(_ptr(nx), _ptr(nz), nx.shape[0], _ptr(A), _ptr(al), _ptr(la),
+                                  _ptr(B), _ptr(be), _ptr(lb), _ptr(w), w.shape[0],
+                                  _ptr(pos), pos.shape[0], _ptr(K), int(threads))
+    if rc != 0:
+        raise ValueError("oracle rejected its input")
+    return K
 
 
 def walker_energies(V, n_walkers: int, n_elec: int) -> np.ndarray:

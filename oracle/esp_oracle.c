@@ -194,6 +194,38 @@ int oracle_potential(const double *nuc_xyz, const double *nuc_Z, int64_t n_nuc,
     return 0;
 }
 
+/*
+ * K[n_pos]: condition of the sum at each position, sum of the absolute values
+ * of its terms: sum_beta |Z_beta / |C - R_beta|| + sum_ab |w_ab (a|1/r_C|b)|.
+ * Same layout and return value as oracle_potential.
+ */
+int oracle_abs_terms(const double *nuc_xyz, const double *nuc_Z, int64_t n_nuc,
+                     const double *A, const double *alpha, const int32_t *la,
+                     const double *B, const double *beta, const int32_t *lb,
+                     const double *w, int64_t n_pairs,
+                     const double *pos, int64_t n_pos, double *K, int n_threads)
+{
+    if (n_nuc < 0 || n_pairs < 0 || n_pos < 0 || (n_pos > 0 && (!pos || !K)))
+        return -1;
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < n_pos; ++i) {
+        const double *C = pos + 3 * i;
+        double acc = 0.0;
+        for (int64_t b = 0; b < n_nuc; ++b) {
+            double dx = C[0] - nuc_xyz[3 * b], dy = C[1] - nuc_xyz[3 * b + 1], dz = C[2] - nuc_xyz[3 * b + 2];
+            acc += fabs(nuc_Z[b] / sqrt(dx * dx + dy * dy + dz * dz));
+        }
+        for (int64_t q = 0; q < n_pairs; ++q)
+            acc += fabs(w[q] * oracle_pair_potential(A + 3 * q, alpha[q], la + 3 * q, B + 3 * q, beta[q], lb + 3 * q, C));
+        K[i] = acc;
+    }
+    return 0;
+}
+
 /* E[w] = -sum_e V[w*n_elec + e]: the walker's environment energy sum_e U_ES(r_e). */
 int oracle_walker_energies(const double *V, int64_t n_walkers, int64_t n_elec, double *E)
 {

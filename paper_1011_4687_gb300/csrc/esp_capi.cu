@@ -5,7 +5,9 @@
 // esp_eval moves only positions in and potentials out.  Device scratch
 // (staged positions, per-split partial sums) is owned by the context and
 // grows on demand.
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/esp.h"
+#include "esp_eval_core.h"
 #include "esp_kernels.h"
 #include "pair_builder.h"
 
@@ -226,7 +229,7 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
         d_pos = static_cast<const double *>(c->in.p);
     }
     Staged stg = staged_view(c, n);
-    if ((e = launch_stage(d_pos, int(n), c->opt.qm_center, stg, s)) != cudaSuccess)
+    if ((e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s)) != cudaSuccess)
         return cuda_fail(e, "staging positions");
     EvalArgs a;
     a.n_pos = int(n);
@@ -305,26 +308,75 @@ void release_all(esp_ctx *c)
         b->release();
 }
 
-template <int L>
-double host_tile(const double *rec, int n, const double *C, const double *boys)
+// Host emulation of the FP32C kernel for one position (one split): the same
+// per-tile core, the same staging, near test and accumulation.
+double host_eval_f32c(const esp_ctx *c, const double *C)
 {
-    constexpr int st = rec64_stride(L);
-    double acc = 0.0;
-    for (int j = 0; j < n; ++j) {
-        const double *r = rec + j * st;
-        double dx = r[0] - C[0], dy = r[1] - C[1], dz = r[2] - C[2];
-        double sp = r[3];
-        double F[L + 1];
-        if constexpr (L == 0) {
-            boys_eval<L, double>((sp * sp) * (dx * dx + dy * dy + dz * dz), boys, F);
-            acc += r[4] * F[0];
-        } else {
-            double x = sp * dx, y = sp * dy, z = sp * dz;
-            boys_eval<L, double>(x * x + y * y + z * z, boys, F);
-            acc += hermite_contract<L, double>(F, x, y, z, r + 4);
-        }
+    const float *boys32 = boys_table32().data();
+    const double *boys64 = boys_table64().data();
+    float ch[1][3], cl[1][3];
+    double c64[1][3];
+    for (int d = 0; d < 3; ++d) {
+        c64[0][d] = C[d];
+        double h = quantize_hi(C[d], c->env.coord_quantum);
+        ch[0][d] = float(h);
+        cl[0][d] = float(C[d] - h);
     }
-    return acc;
+    float S[1] = {0.0f}, Cc[1] = {0.0f};
+    double acc64[1] = {0.0};
+    const float near_r = float(c->opt.near_radius < 0.0 ? 1.5 : c->opt.near_radius);
+    for (const TileMeta &m : c->env.tiles) {
+        if (m.cls == kClassPoint) {
+            tile_points_f64<1>(c->env.rec64.data() + m.off64, m.n, c64, acc64);
+            continue;
+        }
+        bool nearq[1], farq;
+        classify_tile(m, ch[0][0], ch[0][1], ch[0][2], near_r, nearq[0], farq);
+        const float *r = c->env.rec32.data() + m.off32;
+#define ESP_TILE(CLS, LL, SH)                                                      \
+    case CLS:                                                                      \
+        if (farq)                                                                  \
+            tile_f32c<LL, 1, true, SH>(r, m.n, ch, cl, nearq, S, Cc, boys32);      \
+        else                                                                       \
+            tile_f32c<LL, 1, false, SH>(r, m.n, ch, cl, nearq, S, Cc, boys32);     \
+        break;
+        switch (m.cls) {
+            ESP_TILE(0, 0, false)
+            ESP_TILE(1, 1, false)
+            ESP_TILE(2, 2, false)
+            ESP_TILE(3, 3, false)
+            ESP_TILE(4, 4, false)
+            ESP_TILE(8, 0, true)
+            ESP_TILE(9, 1, true)
+            ESP_TILE(10, 2, true)
+            ESP_TILE(11, 3, true)
+            default:
+            ESP_TILE(12, 4, true)
+        }
+#undef ESP_TILE
+        if (nearq[0])
+            acc64[0] += tile_f64_one_any(m.cls, c->env.rec64.data() + m.off64, m.n, C[0], C[1], C[2], boys64);
+    }
+    return (double(S[0]) + double(Cc[0])) + acc64[0];
+}
+
+double host_eval_f64(const esp_ctx *c, const double *C)
+{
+    const double *boys = boys_table64().data();
+    double s = 0.0, cc = 0.0;
+    for (const TileMeta &m : c->env.tiles) {
+        const double *r = c->env.rec64.data() + m.off64;
+        double v;
+        if (m.cls == kClassPoint) {
+            double c64[1][3] = {{C[0], C[1], C[2]}}, acc[1] = {0.0};
+            tile_points_f64<1>(r, m.n, c64, acc);
+            v = acc[0];
+        } else {
+            v = tile_f64_one_any(m.cls, r, m.n, C[0], C[1], C[2], boys);
+        }
+        two_sum_acc(s, cc, v);
+    }
+    return s + cc;
 }
 
 } // namespace
@@ -626,33 +678,11 @@ esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int6
         return fail(ESP_ERR_INVALID, "bad arguments");
     if (!ctx->host_copy)
         return fail(ESP_ERR_UNSUPPORTED, "host copy of the records was dropped (environment too large)");
-    const double *boys = boys_table64().data();
-    const double *rec = ctx->env.rec64.data();
     for (int64_t i = 0; i < n; ++i) {
         double C[3];
         for (int d = 0; d < 3; ++d)
             C[d] = positions[3 * i + d] - ctx->opt.qm_center[d];
-        double s = 0.0, cc = 0.0;
-        for (const TileMeta &m : ctx->env.tiles) {
-            const double *r = rec + m.off64;
-            double v = 0.0;
-            switch (m.cls) {
-            case 0: v = host_tile<0>(r, m.n, C, boys); break;
-            case 1: v = host_tile<1>(r, m.n, C, boys); break;
-            case 2: v = host_tile<2>(r, m.n, C, boys); break;
-            case 3: v = host_tile<3>(r, m.n, C, boys); break;
-            case 4: v = host_tile<4>(r, m.n, C, boys); break;
-            default:
-                for (int j = 0; j < m.n; ++j) {
-                    double dx = r[4 * j] - C[0], dy = r[4 * j + 1] - C[1], dz = r[4 * j + 2] - C[2];
-                    v += r[4 * j + 3] / std::sqrt(dx * dx + dy * dy + dz * dz);
-                }
-            }
-            double t = s + v, bp = t - s;
-            cc += (s - (t - bp)) + (v - bp);
-            s = t;
-        }
-        V_out[i] = s + cc;
+        V_out[i] = ctx->opt.precision == ESP_FP32C ? host_eval_f32c(ctx, C) : host_eval_f64(ctx, C);
     }
     return ESP_OK;
 }

@@ -1,0 +1,192 @@
+// Per-tile evaluation cores shared by the CUDA kernels and the host test hook.
+//
+// One definition serves both, so the host emulation of a kernel performs the
+// same operations in the same order (the device may fuse a*b+c into one FMA
+// where the host rounds twice; the statistics of the errors are the same).
+#pragma once
+
+#include "esp_internal.h"
+
+namespace esp {
+
+#ifndef ESP_SUM_BLOCK
+#define ESP_SUM_BLOCK 16
+#endif
+// distributions summed in plain FP32 before a TwoSum into the running pair
+constexpr int kSumBlock = ESP_SUM_BLOCK;
+
+// error-free S + x = s + e (Knuth TwoSum); e is added into the compensation C
+ESP_HD void two_sum_acc(float &S, float &C, float x)
+{
+    float s = S + x;
+    float bp = s - S;
+    float e = (S - (s - bp)) + (x - bp);
+    S = s;
+    C += e;
+}
+
+ESP_HD void two_sum_acc(double &S, double &C, double x)
+{
+    double s = S + x;
+    double bp = s - S;
+    double e = (S - (s - bp)) + (x - bp);
+    S = s;
+    C += e;
+}
+
+// One distribution (FP64 record [Px, Py, Pz, sqrt(p), G...]) at one position.
+// SHORT: the monopole Q/|P - C| (Q = G_000 sqrt(pi)/(2 sqrt(p))) is left out
+// because the point charge at P carries it.
+template <int L, bool SHORT = false>
+ESP_HD double dist_f64(const double *__restrict__ r, double cx, double cy, double cz,
+                       const double *__restrict__ boys64)
+{
+    double dx = r[0] - cx, dy = r[1] - cy, dz = r[2] - cz;
+    double sp = r[3];
+    double F[L + 1];
+    double v;
+    if constexpr (L == 0) {
+        double T = (sp * sp) * (dx * dx + dy * dy + dz * dz);
+        boys_eval<L, double>(T, boys64, F);
+        v = r[4] * F[0];
+    } else {
+        double x = sp * dx, y = sp * dy, z = sp * dz;
+        double T = x * x + y * y + z * z;
+        boys_eval<L, double>(T, boys64, F);
+        v = hermite_contract<L, double>(F, x, y, z, r + 4);
+    }
+    if constexpr (SHORT)
+        v -= r[4] * 0.88622692545275801365 / sp * esp_rsqrt(dx * dx + dy * dy + dz * dz);
+    return v;
+}
+
+// A whole tile of one class at one position in FP64.
+template <int L, bool SHORT>
+ESP_HD double tile_f64_one(const double *__restrict__ rec, int n, double cx, double cy, double cz,
+                           const double *__restrict__ boys64)
+{
+    constexpr int st = rec64_stride(L);
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j)
+        acc += dist_f64<L, SHORT>(rec + j * st, cx, cy, cz, boys64);
+    return acc;
+}
+
+// cls: tile class (L, possibly with kClassShortBit)
+ESP_HD double tile_f64_one_any(int cls, const double *rec, int n, double cx, double cy, double cz,
+                               const double *boys64)
+{
+    switch (cls) {
+    case 0: return tile_f64_one<0, false>(rec, n, cx, cy, cz, boys64);
+    case 1: return tile_f64_one<1, false>(rec, n, cx, cy, cz, boys64);
+    case 2: return tile_f64_one<2, false>(rec, n, cx, cy, cz, boys64);
+    case 3: return tile_f64_one<3, false>(rec, n, cx, cy, cz, boys64);
+    case 4: return tile_f64_one<4, false>(rec, n, cx, cy, cz, boys64);
+    case 8: return tile_f64_one<0, true>(rec, n, cx, cy, cz, boys64);
+    case 9: return tile_f64_one<1, true>(rec, n, cx, cy, cz, boys64);
+    case 10: return tile_f64_one<2, true>(rec, n, cx, cy, cz, boys64);
+    case 11: return tile_f64_one<3, true>(rec, n, cx, cy, cz, boys64);
+    default: return tile_f64_one<4, true>(rec, n, cx, cy, cz, boys64);
+    }
+}
+
+// Point charges [x, y, z, Z] at PPT positions in FP64.
+template <int PPT>
+ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double (&c64)[PPT][3], double (&acc)[PPT])
+{
+    for (int j = 0; j < n; ++j) {
+        const double *a = pts + 4 * j;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            double dx = a[0] - c64[q][0], dy = a[1] - c64[q][1], dz = a[2] - c64[q][2];
+            acc[q] += a[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32-compensated tiles of class L at PPT positions (record layout in
+// esp_internal.h).  The centre carries a low word, and the offset is formed as
+//   offset = (P_hi - C_hi) + (P_lo - C_lo),
+// so that the fixed rounding of stored coordinates does not add up coherently
+// over the electrons of a walker; the leading coefficient carries a low word
+// for the same reason.  Terms are summed in FP32 over blocks of 16
+// distributions and each block sum is added into a per-position (S, C) pair by
+// TwoSum.  Positions flagged near add nothing here (the caller evaluates the
+// tile for them in FP64).
+//
+// FAR:   every position of the warp is in the asymptotic regime
+//        (p_min * dist^2 >= Tmax): v = sum_tuv M_tuv d^{tuv}(1/|P - C|).
+// !FAR:  general form sum_tuv G_tuv S^0_tuv with the Boys function from the
+//        Taylor table or the asymptotic series per evaluation.
+// SHORT: the monopole sits in the point charge at P (M_000 is stored as 0 for
+//        the far form; the general form uses F_0 - F_0^asymptotic).
+// ---------------------------------------------------------------------------
+template <int L, int PPT, bool FAR, bool SHORT>
+ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[PPT][3], const float (&cl)[PPT][3],
+                      const bool (&nearq)[PPT], float (&S)[PPT], float (&Cc)[PPT], const float *__restrict__ s_boys)
+{
+    constexpr int st = rec32_stride(L);
+    constexpr int nh = num_hermite(L);
+    constexpr int lo = rec32_lo(L);
+    constexpr int co = FAR ? rec32_m(L) : rec32_g(L);
+    constexpr int c0lo = FAR ? rec32_lo(L) + 3 : rec32_g0lo(L);
+    for (int j0 = 0; j0 < n; j0 += kSumBlock) {
+        float blk[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q)
+            blk[q] = 0.0f;
+        const int j1 = (j0 + kSumBlock < n) ? j0 + kSumBlock : n;
+        for (int j = j0; j < j1; ++j) {
+            const float *r = s_rec + j * st;
+            const float px = r[0], py = r[1], pz = r[2], ps = r[3];
+            const float plx = r[lo], ply = r[lo + 1], plz = r[lo + 2], k0lo = r[c0lo];
+            float K[nh];
+#pragma unroll
+            for (int h = 0; h < nh; ++h)
+                K[h] = r[co + h];
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                float dx = (px - ch[q][0]) + (plx - cl[q][0]);
+                float dy = (py - ch[q][1]) + (ply - cl[q][1]);
+                float dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+                float v;
+                float F[L + 1];
+                if constexpr (FAR) {
+                    boys_far<L, float>(dx * dx + dy * dy + dz * dz, F);
+                    v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
+                } else if constexpr (L == 0) {
+                    float T = ps * (dx * dx + dy * dy + dz * dz);
+                    if constexpr (SHORT)
+                        F[0] = boys_f0_short<float>(T);
+                    else
+                        boys_eval<L, float>(T, s_boys, F);
+                    v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
+                } else {
+                    float x = ps * dx, y = ps * dy, z = ps * dz;
+                    float T = x * x + y * y + z * z;
+                    boys_eval<L, float>(T, s_boys, F);
+                    if constexpr (SHORT)
+                        F[0] = boys_f0_short<float>(T);
+                    v = hermite_contract<L, float>(F, x, y, z, K, k0lo);
+                }
+                blk[q] += nearq[q] ? 0.0f : v;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q)
+            two_sum_acc(S[q], Cc[q], blk[q]);
+    }
+}
+
+// Per-position classification of a tile: near (FP64 instead) and far (the
+// asymptotic form is exact to FP32 for every distribution of the tile).
+ESP_HD void classify_tile(const TileMeta &m, float cx, float cy, float cz, float near_r, bool &nearq, bool &farq)
+{
+    float ex = cx - m.cx, ey = cy - m.cy, ez = cz - m.cz;
+    float d = sqrtf(ex * ex + ey * ey + ez * ez) - m.rad;
+    nearq = d < near_r;
+    farq = nearq || (d > 0.0f && m.pmin * d * d >= kBoys32Tmax);
+}
+
+} // namespace esp

@@ -28,10 +28,25 @@ namespace esp {
 
 constexpr int kMaxL = 4;
 constexpr int kClassPoint = 5;          // tile class of point charges
+// Tile class bit: the distributions are centred on a point charge whose FP64
+// charge already includes their monopoles, so the tile holds only the
+// short-range remainder V_d - Q_d/|P - C| (Q_d = (pi/p)^{3/2} D_000).
+constexpr int kClassShortBit = 8;
 ESP_HD constexpr int num_hermite(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
 
-// FP32 record stride (floats): [Px, Py, Pz, p or sqrt(p), G_0 .. G_{n-1}], padded to 4.
-ESP_HD constexpr int rec32_stride(int L) { return L == 0 ? 8 : ((4 + (L == 1 ? 4 : L == 2 ? 10 : L == 3 ? 20 : 35) + 3) / 4) * 4; }
+// FP32 record (floats), L = total angular momentum, n = num_hermite(L):
+//   [0..3]          Px_hi, Py_hi, Pz_hi, p (L = 0) or sqrt(p) (L > 0)
+//   [4..7]          Px_lo, Py_lo, Pz_lo, M_0 lo word
+//   [8, 8+n)        M_tuv = (pi/p)^{3/2} D_tuv   (far-field multipole moments)
+//   [8+n]           G_0 lo word
+//   [9+n, 9+2n)     G_tuv                        (general form, see above)
+// padded to a multiple of 4 floats.
+ESP_HD constexpr int rec32_lo(int) { return 4; }
+ESP_HD constexpr int rec32_m(int) { return 8; }
+ESP_HD constexpr int rec32_g0lo(int L) { return 8 + (L + 1) * (L + 2) * (L + 3) / 6; }
+ESP_HD constexpr int rec32_g(int L) { return 9 + (L + 1) * (L + 2) * (L + 3) / 6; }
+ESP_HD constexpr int rec32_stride(int L) { return ((9 + 2 * ((L + 1) * (L + 2) * (L + 3) / 6) + 3) / 4) * 4; }
+constexpr int kRec32MaxStride = 80;
 // FP64 record stride (doubles): [Px, Py, Pz, sqrt(p), G_0 .. G_{n-1}], padded to 2.
 ESP_HD constexpr int rec64_stride(int L) { return ((4 + (L == 0 ? 1 : L == 1 ? 4 : L == 2 ? 10 : L == 3 ? 20 : 35) + 1) / 2) * 2; }
 constexpr int kPointStride64 = 4;        // [x, y, z, Z]
@@ -116,14 +131,28 @@ ESP_HD double esp_rsqrt(double x)
 #endif
 }
 
+ESP_HD float esp_fma(float a, float b, float c) { return fmaf(a, b, c); }
+ESP_HD double esp_fma(double a, double b, double c) { return fma(a, b, c); }
+
+// x * k with the constant k carried as hi + lo words, rounded once:
+// fma(x, hi, x * lo).  Adding x * lo after rounding x * hi would be lost to
+// that rounding and leave the one-signed error of k in every term (a bias).
+template <typename R>
+ESP_HD R mul_const(R x, double k)
+{
+    const R hi = R(k);
+    const R lo = R(k - double(hi));
+    return esp_fma(x, hi, x * lo);
+}
+
 template <int L, typename R>
 ESP_HD void boys_eval(R T, const R *__restrict__ tab, R (&F)[L + 1])
 {
     using C = BoysConst<R>;
     if (T >= C::tmax()) {
         R rs = esp_rsqrt(T);
-        F[0] = R(0.88622692545275801365) * rs; // sqrt(pi)/2
-        R h = R(0.5) * rs * rs;                // 1/(2T)
+        F[0] = mul_const(rs, 0.88622692545275801365); // sqrt(pi)/2 / sqrt(T)
+        R h = R(0.5) * rs * rs;                         // 1/(2T)
 #pragma unroll
         for (int n = 1; n <= L; ++n)
             F[n] = F[n - 1] * (R(2 * n - 1) * h);
@@ -147,20 +176,52 @@ ESP_HD void boys_eval(R T, const R *__restrict__ tab, R (&F)[L + 1])
             R T2 = T + T;
 #pragma unroll
             for (int n = L - 1; n >= 0; --n)
-                F[n] = (T2 * F[n + 1] + e) * R(1.0 / (2 * n + 1));
+                F[n] = mul_const(T2 * F[n + 1] + e, 1.0 / (2 * n + 1));
         }
     }
+}
+
+ESP_HD float esp_erfc(float x) { return erfcf(x); }
+ESP_HD double esp_erfc(double x) { return erfc(x); }
+
+// F_0(T) - sqrt(pi)/(2 sqrt(T)) = -sqrt(pi)/2 erfc(sqrt(T))/sqrt(T): the part of
+// F_0 left after the monopole moved to a point charge, formed without
+// cancellation; zero to working precision at and above Tmax.
+template <typename R>
+ESP_HD R boys_f0_short(R T)
+{
+    if (T >= BoysConst<R>::tmax())
+        return R(0);
+    R rs = esp_rsqrt(T);
+    return -mul_const(esp_erfc(T * rs) * rs, 0.88622692545275801365);
+}
+
+// Far-field Boys values in units of sqrt(pi)/2 and for unit exponent:
+// Fh_0 = 1/sqrt(r2), Fh_n = Fh_{n-1} (2n-1) / (2 r2).  With these, the
+// recursion below evaluated at the unscaled offset P - C gives the Cartesian
+// derivatives of 1/|P - C| (the exact potential of a Hermite Gaussian once
+// exp(-p|P-C|^2) is negligible), and the multipole moments M_tuv complete it.
+template <int L, typename R>
+ESP_HD void boys_far(R r2, R (&F)[L + 1])
+{
+    R rs = esp_rsqrt(r2);
+    F[0] = rs;
+    R h = R(0.5) * rs * rs;
+#pragma unroll
+    for (int n = 1; n <= L; ++n)
+        F[n] = F[n - 1] * (R(2 * n - 1) * h);
 }
 
 // ---------------------------------------------------------------------------
 // sum_tuv G_tuv S^0_tuv for one distribution of total angular momentum L at
 // scaled offset (x, y, z) = sqrt(p) (P - C), given F_0..F_L(T).
 // ---------------------------------------------------------------------------
+// g0lo is the low word of G_0: the leading product is rounded once with it.
 template <int L, typename R>
-ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const R *__restrict__ G)
+ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const R *__restrict__ G, R g0lo = R(0))
 {
     if constexpr (L == 0) {
-        return G[0] * F[0];
+        return esp_fma(G[0], F[0], g0lo * F[0]);
     } else {
     // S[n][h] for levels n = 0..L; level n needs N <= L - n
     R S[L + 1][35];
@@ -197,10 +258,10 @@ ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const R *__restric
             }
         }
     }
-    R acc = G[0] * S[0][0];
+    R acc = esp_fma(G[0], S[0][0], g0lo * S[0][0]);
 #pragma unroll
     for (int h = 1; h < num_hermite(L); ++h)
-        acc += G[h] * S[0][h];
+        acc = esp_fma(G[h], S[0][h], acc);
     return acc;
     }
 }

@@ -7,9 +7,9 @@
 
 namespace esp {
 
-// Recentred positions, structure of arrays: FP64 copy and FP32 hi + lo split
-// (hi = fp32(x), lo = fp32(x - hi)), so FP32 code can form P - C without
-// losing the low bits of C.
+// Recentred positions, structure of arrays: FP64 copy and FP32 hi + lo split,
+// hi on the environment's coordinate grid and lo = fp32(x - hi), so FP32 code
+// forms P - C as (P_hi - C_hi) + (P_lo - C_lo) with an exact first difference.
 struct Staged {
     double *x64, *y64, *z64;
     float *xh, *yh, *zh, *xl, *yl, *zl;
@@ -30,7 +30,7 @@ struct EvalArgs {
     float near_r;     // FP32C: FP64 re-evaluation radius around a tile's bounding sphere
 };
 
-cudaError_t launch_stage(const double *pos_in, int n, const double center[3], const Staged &st,
+cudaError_t launch_stage(const double *pos_in, int n, const double center[3], double quantum, const Staged &st,
                          cudaStream_t s);
 // precision: 0 = FP64, 1 = FP32C.  threads in {64, 128, 256}, ppt in {1, 2, 4}.
 cudaError_t launch_potential(int precision, const EvalArgs &a, int threads, int ppt, cudaStream_t s);

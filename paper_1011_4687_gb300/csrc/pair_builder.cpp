@@ -16,7 +16,8 @@
 //   4. screen: drop the distribution when its absolute-charge bound
 //        sum_tuv |D_tuv| int |Lambda_tuv| dr = sum |D_tuv| p^{(t+u+v-3)/2} h_t h_u h_v,
 //      h_t = int |H_t(y)| e^{-y^2} dy, is below screen_tol;
-//   5. scale G_tuv = (2 pi / p) p^{(t+u+v)/2} D_tuv (see esp_internal.h);
+//   5. scale G_tuv = (2 pi / p) p^{(t+u+v)/2} D_tuv and the far-field moments
+//      M_tuv = (pi/p)^{3/2} D_tuv (see esp_internal.h);
 //   6. class by L, band by exponent (factors of 4 in p), Morton order of P
 //      inside a band, and cut into tiles with a bounding sphere each.
 #include "pair_builder.h"
@@ -26,6 +27,7 @@
 #include <cstring>
 #include <mutex>
 #include <numeric>
+#include <unordered_map>
 
 namespace esp {
 
@@ -194,7 +196,10 @@ struct Dist {
     double P[3];
     double p;
     int L;
+    bool onsite;   // A == B: centred exactly on P = A
+    bool shortr;   // monopole moved into the point charge at P
     double G[35];
+    double M[35];
     double qabs;
     uint64_t key;
 };
@@ -390,6 +395,7 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
                     int v = N - t - u, h = hidx(t, u, v);
                     qabs += std::fabs(D[h]) * std::pow(p, 0.5 * (N - 3)) * habs[t] * habs[u] * habs[v];
                     ds.G[h] = 2.0 * kPi / p * std::pow(p, 0.5 * N) * D[h];
+                    ds.M[h] = std::pow(kPi / p, 1.5) * D[h];
                 }
         g0 = g1;
         if (qabs < opt.screen_tol || qabs == 0.0) {
@@ -398,10 +404,76 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         }
         for (int d = 0; d < 3; ++d)
             ds.P[d] = P[d];
+        ds.onsite = o.A[0] == o.B[0] && o.A[1] == o.B[1] && o.A[2] == o.B[2];
+        if (ds.onsite)
+            for (int d = 0; d < 3; ++d)
+                ds.P[d] = o.A[d];
+        ds.shortr = false;
         ds.p = p;
         ds.L = L;
         ds.qabs = qabs;
         dist.push_back(ds);
+    }
+
+    // Point charges (recentred).  On-site distributions (A == B) that sit on a
+    // point charge, or that share their centre with at least 8 others, hand
+    // their monopole Q_d = M_000 to a point charge at that centre; they keep
+    // only the short-range remainder V_d - Q_d/|P - C|.  The many on-site
+    // distributions of one atom otherwise share one rounded FP32 value of
+    // 1/|P - C| and their errors add up coherently.
+    struct PointQ {
+        double x[3];
+        double Z;
+    };
+    std::vector<PointQ> pts;
+    pts.reserve(size_t(n_charges) + 16);
+    for (int64_t i = 0; i < n_charges; ++i) {
+        PointQ q;
+        for (int d = 0; d < 3; ++d)
+            q.x[d] = charges[i].xyz[d] - qc[d];
+        q.Z = charges[i].Z;
+        pts.push_back(q);
+    }
+    {
+        auto ckey = [](const double *x) {
+            uint64_t k = 1469598103934665603ull;
+            for (int d = 0; d < 3; ++d) {
+                uint64_t b;
+                std::memcpy(&b, &x[d], 8);
+                k = (k ^ b) * 1099511628211ull;
+            }
+            return k;
+        };
+        std::unordered_map<uint64_t, int64_t> at_point;
+        for (size_t i = 0; i < pts.size(); ++i)
+            at_point.emplace(ckey(pts[i].x), int64_t(i));
+        std::unordered_map<uint64_t, std::vector<size_t>> groups;
+        for (size_t k = 0; k < dist.size(); ++k)
+            if (dist[k].onsite)
+                groups[ckey(dist[k].P)].push_back(k);
+        const double c0 = 0.88622692545275801365; // sqrt(pi)/2
+        for (auto &g : groups) {
+            const Dist &d0 = dist[g.second[0]];
+            auto it = at_point.find(g.first);
+            bool on_point = it != at_point.end() && pts[size_t(it->second)].x[0] == d0.P[0] &&
+                            pts[size_t(it->second)].x[1] == d0.P[1] && pts[size_t(it->second)].x[2] == d0.P[2];
+            if (!on_point && g.second.size() < 8)
+                continue;
+            double Q = 0.0;
+            for (size_t k : g.second) {
+                Q += dist[k].G[0] * c0 / std::sqrt(dist[k].p);
+                dist[k].shortr = true;
+            }
+            if (on_point) {
+                pts[size_t(it->second)].Z += Q;
+            } else {
+                PointQ q;
+                for (int d = 0; d < 3; ++d)
+                    q.x[d] = d0.P[d];
+                q.Z = Q;
+                pts.push_back(q);
+            }
+        }
     }
 
     // order: class L, exponent band (factor 4), Morton code of P
@@ -423,48 +495,55 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
     for (Dist &d : dist) {
         int band = int(std::floor(std::log(d.p) / std::log(4.0))) + 64;
         band = std::min(std::max(band, 0), 127);
-        d.key = (uint64_t(d.L) << 40) | (uint64_t(band) << 32) | morton(d.P, lo, inv);
+        d.key = (uint64_t(d.L) << 41) | (uint64_t(d.shortr) << 40) | (uint64_t(band) << 32) | morton(d.P, lo, inv);
     }
     std::stable_sort(dist.begin(), dist.end(), [](const Dist &a, const Dist &b) { return a.key < b.key; });
 
     out = HostEnv();
     out.tile_size = tile;
+    // Coordinate grid: offsets P - C stay below 4 max|P| for positions inside the
+    // environment's extent, so 2^24 q >= 4 max|P| keeps P_hi - C_hi exact.
+    {
+        double m = 1.0;
+        for (int k = 0; k < 3; ++k)
+            m = std::max(m, std::max(std::fabs(lo[k]), std::fabs(hi[k])));
+        out.coord_quantum = std::ldexp(1.0, int(std::ceil(std::log2(4.0 * m))) - 24);
+    }
     out.n_pairs_in = n_pairs;
     out.n_distributions = int64_t(dist.size());
     out.n_screened = screened;
 
     // point-charge tiles (FP64 records [x, y, z, Z]), Morton order
+    const int64_t n_pts = int64_t(pts.size());
     std::vector<int64_t> pidx{};
-    pidx.resize(size_t(n_charges));
+    pidx.resize(size_t(n_pts));
     std::iota(pidx.begin(), pidx.end(), 0);
     std::vector<uint64_t> pkey{};
-    pkey.resize(size_t(n_charges));
-    for (int64_t i = 0; i < n_charges; ++i) {
-        double P[3] = {charges[i].xyz[0] - qc[0], charges[i].xyz[1] - qc[1], charges[i].xyz[2] - qc[2]};
-        pkey[size_t(i)] = morton(P, lo, inv);
-    }
+    pkey.resize(size_t(n_pts));
+    for (int64_t i = 0; i < n_pts; ++i)
+        pkey[size_t(i)] = morton(pts[size_t(i)].x, lo, inv);
     std::stable_sort(pidx.begin(), pidx.end(), [&](int64_t a, int64_t b) { return pkey[size_t(a)] < pkey[size_t(b)]; });
     int64_t kept_charges = 0;
-    for (int64_t i = 0; i < n_charges; ++i)
-        kept_charges += charges[pidx[size_t(i)]].Z != 0.0;
+    for (int64_t i = 0; i < n_pts; ++i)
+        kept_charges += pts[size_t(i)].Z != 0.0;
     out.n_point_charges = kept_charges;
 
     size_t off64 = 0, off32 = 0;
     std::vector<double> pbuf;
-    for (int64_t s = 0; s < n_charges;) {
+    for (int64_t s = 0; s < n_pts;) {
         TileMeta m;
         std::memset(&m, 0, sizeof(m));
         m.cls = kClassPoint;
         m.off64 = int32_t(off64);
         pbuf.clear();
         double qsum = 0.0;
-        while (s < n_charges && m.n < tile) {
-            const esp_point_charge &c = charges[pidx[size_t(s)]];
+        while (s < n_pts && m.n < tile) {
+            const PointQ &c = pts[size_t(pidx[size_t(s)])];
             ++s;
             if (c.Z == 0.0)
                 continue;
             for (int d = 0; d < 3; ++d)
-                pbuf.push_back(c.xyz[d] - qc[d]);
+                pbuf.push_back(c.x[d]);
             pbuf.push_back(c.Z);
             qsum += std::fabs(c.Z);
             ++m.n;
@@ -486,11 +565,12 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         while (e < dist.size() && e - s < size_t(tile) && (dist[e].key >> 32) == grp)
             ++e;
         const int L = dist[s].L;
+        const bool shortr = dist[s].shortr;
         const int nh = num_hermite(L);
         const int st32 = rec32_stride(L), st64 = rec64_stride(L);
         TileMeta m;
         std::memset(&m, 0, sizeof(m));
-        m.cls = L;
+        m.cls = L | (shortr ? kClassShortBit : 0);
         m.n = int32_t(e - s);
         m.off32 = int32_t(off32);
         m.off64 = int32_t(off64);
@@ -505,12 +585,17 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
             out.n_by_L[L] += 1;
             size_t b32 = out.rec32.size();
             out.rec32.resize(b32 + st32, 0.0f);
-            out.rec32[b32 + 0] = float(d.P[0]);
-            out.rec32[b32 + 1] = float(d.P[1]);
-            out.rec32[b32 + 2] = float(d.P[2]);
+            for (int c = 0; c < 3; ++c)
+                out.rec32[b32 + c] = float(quantize_hi(d.P[c], out.coord_quantum));
             out.rec32[b32 + 3] = L == 0 ? float(d.p) : float(std::sqrt(d.p));
-            for (int h = 0; h < nh; ++h)
-                out.rec32[b32 + 4 + h] = float(d.G[h]);
+            for (int c = 0; c < 3; ++c)
+                out.rec32[b32 + rec32_lo(L) + c] = float(d.P[c] - quantize_hi(d.P[c], out.coord_quantum));
+            out.rec32[b32 + rec32_lo(L) + 3] = shortr ? 0.0f : float(d.M[0] - double(float(d.M[0])));
+            out.rec32[b32 + rec32_g0lo(L)] = float(d.G[0] - double(float(d.G[0])));
+            for (int h = 0; h < nh; ++h) {
+                out.rec32[b32 + rec32_m(L) + h] = (shortr && h == 0) ? 0.0f : float(d.M[h]);
+                out.rec32[b32 + rec32_g(L) + h] = float(d.G[h]);
+            }
             size_t b64 = out.rec64.size();
             out.rec64.resize(b64 + st64, 0.0);
             out.rec64[b64 + 0] = d.P[0];

@@ -1,6 +1,7 @@
 // Host pair builder: environment input -> tiled Hermite distributions.
 #pragma once
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -19,7 +20,14 @@ struct HostEnv {
     int64_t n_screened = 0;
     int64_t n_by_L[kMaxL + 1] = {0, 0, 0, 0, 0};
     int tile_size = 128;
+    // Grid of the FP32 high words of coordinates (a power of two): centres and
+    // positions are split as x = hi + lo with hi a multiple of coord_quantum, so
+    // P_hi - C_hi is exact in FP32 whenever |P_hi - C_hi| < 2^24 * coord_quantum.
+    double coord_quantum = 1.0 / 1048576.0;
 };
+
+// hi word of x on the grid q (exact in double and in FP32 for |x| < 2^23 q)
+inline double quantize_hi(double x, double q) { return std::nearbyint(x / q) * q; }
 
 // Validate, fold, screen, sort and tile.  Returns ESP_OK or ESP_ERR_INVALID
 // (with a message in err).

@@ -3,7 +3,10 @@
 Tolerances (written here, derived in the design doc):
   FP64 path : |V - V_oracle| <= 1e-10 * max(|V_oracle|, 1 Ha/e) per point;
   FP32C path: |V - V_oracle| <= 2e-6 Ha/e per point and
-              |E_w - E_w,oracle| <= 1e-5 Ha per walker (E_w = -sum_e V).
+              |E_w - E_w,oracle| <= 1e-5 Ha per walker (E_w = -sum_e V);
+              in the synthetic p/d environments, where positions sit inside
+              large charges, the per-point bound is max(2e-6, 1.2e-7 * kappa)
+              with kappa = sum of |terms| (two FP32 ulps of the sum's condition).
 Sizes span several tiles and a ragged tail; the full-size realistic case runs
 in the benchmark's launch configuration and is checked on sampled positions.
 """
@@ -22,6 +25,7 @@ pytestmark = pytest.mark.gpu
 FP64_REL = 1e-10
 FP32_POINT = 2e-6
 FP32_WALKER = 1e-5
+FP32_KAPPA = 1.2e-7
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,9 +43,10 @@ def check_fp64(V, ref, what=""):
     assert np.all(err <= lim), "%s: worst %.3e (limit %.1e) at %d" % (what, err.max(), FP64_REL, int(np.argmax(err / lim)))
 
 
-def check_fp32(V, ref, what=""):
+def check_fp32(V, ref, what="", kappa=None):
     err = np.abs(V - ref)
-    assert err.max() <= FP32_POINT, "%s: worst per-point error %.3e Ha" % (what, err.max())
+    lim = FP32_POINT if kappa is None else np.maximum(FP32_POINT, FP32_KAPPA * kappa)
+    assert np.all(err <= lim), "%s: worst per-point error %.3e Ha" % (what, err.max())
 
 
 def env_of(wl, precision, **kw):
@@ -94,6 +99,7 @@ def test_pd_environment_ragged(n_pos, shape):
     wl = tiny_pd_environment(500 + n_pos, n_pairs=700, n_nuclei=40, n_pos=n_pos, exp_range=(0.1, 80.0),
                              spread=3.0, pos_radius=4.0)
     ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    kappa = oracle.abs_terms(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
     kw = dict(SHAPES[shape])
     for prec in ("fp64", "fp32c"):
         k = dict(kw)
@@ -101,7 +107,10 @@ def test_pd_environment_ragged(n_pos, shape):
             k["positions_per_thread"] = 2
         with env_of(wl, prec, screen_tol=0.0, **k) as env:
             V = env.eval(wl.positions)
-        (check_fp64 if prec == "fp64" else check_fp32)(V, ref, "%s n=%d %s" % (prec, n_pos, kw))
+        if prec == "fp64":
+            check_fp64(V, ref, "fp64 n=%d %s" % (n_pos, kw))
+        else:
+            check_fp32(V, ref, "fp32c n=%d %s" % (n_pos, kw), kappa)
 
 
 # ---------------------------------------------------------------------------
@@ -183,7 +192,7 @@ def test_point_cells(n_pos):
 # ---------------------------------------------------------------------------
 def test_host_and_device_pointers_agree_and_repeat_bitwise():
     torch = pytest.importorskip("torch")
-    wl = tiny_pd_environment(42, n_pairs=300, n_nuclei=20, n_pos=777, spread=3.0)
+    wl = tiny_pd_environment(42, n_pairs=300, n_nuclei=20, n_pos=777, spread=3.0)  # bitwise checks only
     for prec in ("fp64", "fp32c"):
         with env_of(wl, prec) as env:
             Vh = env.eval(wl.positions)
@@ -220,21 +229,23 @@ def test_empty_and_degenerate_inputs():
 def test_memory_space_mismatch_rejected():
     torch = pytest.importorskip("torch")
     wl = tiny_pd_environment(11, n_pairs=5, n_nuclei=2, n_pos=4)
+    kappa = oracle.abs_terms(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
     with env_of(wl, "fp32c") as env:
         with pytest.raises(esp.EspError) as ei:
             env.eval(torch.from_numpy(wl.positions).cuda(), out=np.zeros(4))
         assert ei.value.status == esp.ESP_ERR_INVALID
         # the context stays usable
         ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
-        check_fp32(env.eval(wl.positions), ref, "after error")
+        check_fp32(env.eval(wl.positions), ref, "after error", kappa)
 
 
 def test_precision_switch_and_timing():
     wl = tiny_pd_environment(12, n_pairs=200, n_nuclei=10, n_pos=300, spread=3.0)
     ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    kappa = oracle.abs_terms(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
     with env_of(wl, "fp32c") as env:
         env.set_timing(True)
-        check_fp32(env.eval(wl.positions), ref)
+        check_fp32(env.eval(wl.positions), ref, "timing", kappa)
         k, t = env.last_timing()
         assert 0.0 < k <= t
         env.set_precision("fp64")

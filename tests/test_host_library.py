@@ -61,15 +61,13 @@ def test_device_boys_algorithm_matches_oracle(lib, prec, rtol):
             assert np.allclose(F, ref[:nmax + 1], rtol=rtol, atol=0), (prec, T, nmax, F, ref)
 
 
-def host_ctx(wl, **kw):
-    return esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, **kw) if False else _host_env(wl, **kw)
-
-
-def _host_env(wl, screen_tol=0.0, tile_size=0):
+def _host_env(wl, screen_tol=0.0, tile_size=0, precision="fp64", near_radius=-1.0):
     lib = esp.load()
     import ctypes
     opt = esp.default_options()
     opt.flags = 1  # ESP_FLAG_HOST_ONLY
+    opt.precision = esp.PRECISIONS[precision]
+    opt.near_radius = near_radius
     opt.screen_tol = screen_tol
     opt.tile_size = tile_size
     opt.qm_center[:] = list(map(float, wl.qm_center))
@@ -200,3 +198,49 @@ def test_host_only_context_refuses_evaluation(lib):
     assert ei.value.status == esp.ESP_ERR_STATE
     env.close()
     esp.load().esp_destroy(None)  # NULL-safe
+
+
+# ---------------------------------------------------------------------------
+# error budget of the FP32-compensated arithmetic (host emulation of the kernel)
+# ---------------------------------------------------------------------------
+def test_fp32c_budget_small_environment(lib):
+    wl = small_environment(n_walkers=10, n_elec=100)
+    env = _host_env(wl, screen_tol=1e-12, precision="fp32c")
+    V = env.debug_host_eval(wl.positions)
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    assert np.abs(V - ref).max() <= 2e-6
+    E = -V.reshape(10, 100).sum(1)
+    Eref = oracle.walker_energies(ref, 10, 100)
+    assert np.abs(E - Eref).max() <= 1e-5
+    # no bias: the mean error is far below the per-point scatter
+    assert abs(np.mean(V - ref)) <= 3e-8
+
+
+def test_fp32c_budget_realistic_environment(lib):
+    from workloads import realistic_environment
+    wl = realistic_environment(seed=7711, n_atoms=200, n_walkers=4, n_elec=32)
+    env = _host_env(wl, screen_tol=1e-12, precision="fp32c")
+    V = env.debug_host_eval(wl.positions)
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    assert np.abs(V - ref).max() <= 2e-6
+    E = -V.reshape(4, 32).sum(1)
+    assert np.abs(E - oracle.walker_energies(ref, 4, 32)).max() <= 1e-5
+
+
+def test_onsite_monopoles_move_to_point_charges(lib):
+    """On-site distributions centred on a nucleus give their monopole to it; the
+    evaluated sum is unchanged (FP64) and the point count does not grow."""
+    from workloads import realistic_environment
+    wl = realistic_environment(seed=99, n_atoms=30, n_walkers=2, n_elec=8)
+    env = _host_env(wl, screen_tol=0.0, precision="fp64")
+    info = env.info()
+    assert info["n_point_charges"] == 30
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    assert np.allclose(env.debug_host_eval(wl.positions), ref, rtol=1e-12, atol=1e-12)
+    env32 = _host_env(wl, screen_tol=0.0, precision="fp32c")
+    assert np.abs(env32.debug_host_eval(wl.positions) - ref).max() <= 2e-6
+    # a position at 1e-3 bohr from a nucleus: the FP64 near path takes the atom
+    C = wl.nuclei_xyz[3] + np.array([1e-3, 0.0, 0.0])
+    r1 = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, C[None])
+    assert np.allclose(env.debug_host_eval(C[None]), r1, rtol=1e-12)
+    assert np.allclose(env32.debug_host_eval(C[None]), r1, rtol=1e-10)
