@@ -104,8 +104,9 @@ typedef struct {
     void *cuda_stream;             /* cudaStream_t for all work; NULL = the default stream */
     int32_t device;                /* CUDA device ordinal; -1 = the current device */
     int32_t tile_size;             /* distributions per tile: 64, 128 or 256; 0 = 128 */
-    int32_t threads_per_block;     /* 0 = tuned default */
-    int32_t positions_per_thread;  /* 0 = tuned default */
+    int32_t threads_per_block;     /* 0 = tuned default; else 64, 128 or 256 */
+    int32_t positions_per_thread;  /* 0 = tuned default; FP32C shapes built: 64x{2,4},
+                                      128x{1,2,4}, 256x{1,2}; FP64 uses min(this, 2) */
     int32_t pair_splits;           /* tiles are dealt round-robin to this many splits per
                                       position block; 0 = chosen from the problem size */
     int32_t flags;                 /* ESP_FLAG_* bits; 0 for normal use */

@@ -475,7 +475,15 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const 
         c->threads[0] = c->threads[1] = opt.threads_per_block;
     }
     if (opt.positions_per_thread) {
-        c->ppt[0] = c->ppt[1] = opt.positions_per_thread;
+        c->ppt[1] = opt.positions_per_thread;
+        c->ppt[0] = std::min(opt.positions_per_thread, 2); // FP64 keeps at most 2 positions per thread
+    }
+    for (int p = 0; p < 2; ++p) {
+        if (!potential_shape_supported(p, c->threads[p], c->ppt[p])) {
+            delete c;
+            return fail(ESP_ERR_INVALID, "launch shape %d threads x %d positions is not built for %s", c->threads[p],
+                        c->ppt[p], p == 0 ? "FP64" : "FP32C");
+        }
     }
     cudaError_t e;
     int64_t bytes = 0;

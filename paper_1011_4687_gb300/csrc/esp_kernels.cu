@@ -261,6 +261,17 @@ cudaError_t launch_with_smem(K kernel, dim3 grid, dim3 block, size_t smem, cudaS
 
 } // namespace
 
+bool potential_shape_supported(int precision, int threads, int ppt)
+{
+    if (precision == 0)
+        return (threads == 64 || threads == 128 || threads == 256) && (ppt == 1 || ppt == 2);
+    if (threads == 64)
+        return ppt == 2 || ppt == 4;
+    if (threads == 128)
+        return ppt == 1 || ppt == 2 || ppt == 4;
+    return threads == 256 && (ppt == 1 || ppt == 2);
+}
+
 size_t potential_smem_bytes(int precision, int tile_size)
 {
     if (precision == 0)
@@ -288,16 +299,20 @@ cudaError_t launch_potential(int precision, const EvalArgs &a, int threads, int 
 #define ESP_LAUNCH(KER, NT, PPT) \
     if (threads == NT && ppt == PPT) return launch_with_smem(KER<NT, PPT>, grid, block, smem, s, a)
     if (precision == 0) {
+        ESP_LAUNCH(potential_f64_kernel, 64, 1);
+        ESP_LAUNCH(potential_f64_kernel, 64, 2);
         ESP_LAUNCH(potential_f64_kernel, 128, 1);
         ESP_LAUNCH(potential_f64_kernel, 128, 2);
         ESP_LAUNCH(potential_f64_kernel, 256, 1);
-        ESP_LAUNCH(potential_f64_kernel, 64, 2);
+        ESP_LAUNCH(potential_f64_kernel, 256, 2);
     } else {
+        ESP_LAUNCH(potential_f32c_kernel, 64, 2);
+        ESP_LAUNCH(potential_f32c_kernel, 64, 4);
         ESP_LAUNCH(potential_f32c_kernel, 128, 1);
         ESP_LAUNCH(potential_f32c_kernel, 128, 2);
         ESP_LAUNCH(potential_f32c_kernel, 128, 4);
+        ESP_LAUNCH(potential_f32c_kernel, 256, 1);
         ESP_LAUNCH(potential_f32c_kernel, 256, 2);
-        ESP_LAUNCH(potential_f32c_kernel, 64, 4);
     }
 #undef ESP_LAUNCH
     return cudaErrorInvalidConfiguration;

@@ -35,6 +35,9 @@ cudaError_t launch_stage(const double *pos_in, int n, const double center[3], do
 // precision: 0 = FP64, 1 = FP32C.  threads in {64, 128, 256}, ppt in {1, 2, 4}.
 cudaError_t launch_potential(int precision, const EvalArgs &a, int threads, int ppt, cudaStream_t s);
 size_t potential_smem_bytes(int precision, int tile_size);
+// Launch shapes compiled into the library: FP64 threads {64,128,256} x ppt {1,2};
+// FP32C (64,{2,4}), (128,{1,2,4}), (256,{1,2}).
+bool potential_shape_supported(int precision, int threads, int ppt);
 cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s);
 cudaError_t launch_walkers(const double *V, int n_walkers, int n_elec, double *E, cudaStream_t s);
 

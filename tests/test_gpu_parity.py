@@ -102,10 +102,7 @@ def test_pd_environment_ragged(n_pos, shape):
     kappa = oracle.abs_terms(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
     kw = dict(SHAPES[shape])
     for prec in ("fp64", "fp32c"):
-        k = dict(kw)
-        if prec == "fp64" and k.get("positions_per_thread") == 4:
-            k["positions_per_thread"] = 2
-        with env_of(wl, prec, screen_tol=0.0, **k) as env:
+        with env_of(wl, prec, screen_tol=0.0, **kw) as env:
             V = env.eval(wl.positions)
         if prec == "fp64":
             check_fp64(V, ref, "fp64 n=%d %s" % (n_pos, kw))
