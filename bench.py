@@ -144,12 +144,15 @@ def profiled_traffic(kernel: str, units: float):
     return e["dram_bytes_per_launch"] * units / e["units_per_launch"]
 
 
-def build_workload(rank: int):
+def build_workload(rank: int, walkers: int = 4096):
     from workloads import realistic_environment, seed_for_config, qm_positions
     wl = realistic_environment(seed=seed_for_config(2))
     if rank > 0:
         rng = np.random.default_rng(seed_for_config(2) * 1000 + rank)
         wl.positions = qm_positions(rng, wl.n_walkers * wl.n_elec)
+    if walkers != wl.n_walkers:
+        wl.positions = wl.positions[: walkers * wl.n_elec].copy()
+        wl.n_walkers = walkers
     return wl
 
 
@@ -202,6 +205,8 @@ def main(argv=None):
     ap.add_argument("--fp64-walkers", type=int, default=256, help="walkers in the FP64 rate measurement")
     ap.add_argument("--ref-positions", type=int, default=32, help="positions per oracle step (reference arm)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
+    ap.add_argument("--walkers", type=int, default=4096,
+                    help="walkers of 32 electrons per GPU (the benchmark workload is 4096; fewer only for profiling)")
     args = ap.parse_args(argv)
     keep_heap()
     if args.impl == "reference":
@@ -223,7 +228,7 @@ def main(argv=None):
         dist.barrier()
     esp.load()
 
-    wl = build_workload(rank)
+    wl = build_workload(rank, args.walkers)
     stream = torch.cuda.current_stream()
     env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
     info = env.info()
@@ -318,7 +323,8 @@ def main(argv=None):
     out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "realistic: 2,000 atoms, cc-pVDZ-shaped primitives, %d distributions + "
+           "config": {"workload": ("" if args.walkers == 4096 else "REDUCED (profiling) ") +
+                                  "realistic: 2,000 atoms, cc-pVDZ-shaped primitives, %d distributions + "
                                   "%d point charges, %d positions (%d walkers x %d electrons) per GPU"
                                   % (info["n_distributions"], info["n_point_charges"], n_pos, wl.n_walkers,
                                      wl.n_elec),

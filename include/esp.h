@@ -112,7 +112,7 @@ typedef struct {
     int32_t flags;                 /* ESP_FLAG_* bits; 0 for normal use */
     double near_radius;            /* FP32C: a (position, tile) block whose distance to the
                                       tile's bounding sphere is below this is evaluated in
-                                      FP64; < 0 = default (1.5 bohr) */
+                                      FP64; < 0 = default (0: off) */
 } esp_options;
 
 /* Per-context facts, for reporting and for counting evaluations. */

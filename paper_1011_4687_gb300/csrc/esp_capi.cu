@@ -243,7 +243,7 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
     a.boys32 = static_cast<const float *>(c->boys32.p);
     a.boys64 = static_cast<const double *>(c->boys64.p);
     a.partial = static_cast<double *>(c->partial.p);
-    a.near_r = float(c->opt.near_radius < 0.0 ? 1.5 : c->opt.near_radius);
+    a.near_r = float(c->opt.near_radius < 0.0 ? kDefaultNearRadius : c->opt.near_radius);
     if (c->timing && (e = cudaEventRecord(c->ev[1], s)) != cudaSuccess)
         return cuda_fail(e, "recording a timing event");
     if (c->n_tiles == 0) {
@@ -324,7 +324,7 @@ double host_eval_f32c(const esp_ctx *c, const double *C)
     }
     float S[1] = {0.0f}, Cc[1] = {0.0f};
     double acc64[1] = {0.0};
-    const float near_r = float(c->opt.near_radius < 0.0 ? 1.5 : c->opt.near_radius);
+    const float near_r = float(c->opt.near_radius < 0.0 ? kDefaultNearRadius : c->opt.near_radius);
     for (const TileMeta &m : c->env.tiles) {
         if (m.cls == kClassPoint) {
             tile_points_f64<1>(c->env.rec64.data() + m.off64, m.n, c64, acc64);

@@ -179,13 +179,14 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
     }
 }
 
-// Per-position classification of a tile: near (FP64 instead) and far (the
-// asymptotic form is exact to FP32 for every distribution of the tile).
+// Per-position classification of a tile: near (FP64 instead; only with a
+// positive near_r) and far (the asymptotic form is exact to FP32 for every
+// distribution of the tile).
 ESP_HD void classify_tile(const TileMeta &m, float cx, float cy, float cz, float near_r, bool &nearq, bool &farq)
 {
     float ex = cx - m.cx, ey = cy - m.cy, ez = cz - m.cz;
     float d = sqrtf(ex * ex + ey * ey + ez * ez) - m.rad;
-    nearq = d < near_r;
+    nearq = near_r > 0.0f && d < near_r;
     farq = nearq || (d > 0.0f && m.pmin * d * d >= kBoys32Tmax);
 }
 

@@ -28,6 +28,9 @@ namespace esp {
 
 constexpr int kMaxL = 4;
 constexpr int kClassPoint = 5;          // tile class of point charges
+// FP64 re-evaluation radius of the FP32C kernel when the caller leaves it unset:
+// off, since nuclei and on-site monopoles are FP64 point charges already.
+constexpr double kDefaultNearRadius = 0.0;
 // Tile class bit: the distributions are centred on a point charge whose FP64
 // charge already includes their monopoles, so the tile holds only the
 // short-range remainder V_d - Q_d/|P - C| (Q_d = (pi/p)^{3/2} D_000).

@@ -247,3 +247,14 @@ def test_precision_switch_and_timing():
         assert 0.0 < k <= t
         env.set_precision("fp64")
         check_fp64(env.eval(wl.positions), ref)
+
+
+def test_fp64_near_path_when_enabled():
+    """With a positive near_radius, (position, tile) blocks closer than it are
+    evaluated in FP64 inside the FP32C kernel; the result stays within the FP32C
+    bounds and moves toward the FP64 value."""
+    wl, ref = realistic_small()
+    with env_of(wl, "fp32c", near_radius=2.0) as env:
+        V, E = env.eval_walkers(wl.positions, wl.n_walkers, wl.n_elec)
+    check_fp32(V, ref, "near 2.0")
+    assert np.abs(E - oracle.walker_energies(ref, wl.n_walkers, wl.n_elec)).max() <= FP32_WALKER
