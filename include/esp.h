@@ -112,7 +112,9 @@ typedef struct {
     int32_t flags;                 /* ESP_FLAG_* bits; 0 for normal use */
     double near_radius;            /* FP32C: a (position, tile) block whose distance to the
                                       tile's bounding sphere is below this is evaluated in
-                                      FP64; < 0 = default (0: off) */
+                                      FP64, for tiles holding a distribution whose potential
+                                      can exceed 2 Ha (a compact charge not merged into a
+                                      point charge); < 0 = default (1.5 bohr), 0 = off */
 } esp_options;
 
 /* Per-context facts, for reporting and for counting evaluations. */
@@ -123,6 +125,7 @@ typedef struct {
     int64_t n_screened;            /* distributions dropped by screen_tol */
     int64_t n_by_L[ESP_MAX_L + 1]; /* distributions per total angular momentum L */
     int64_t n_tiles;               /* tiles of distributions and of point charges */
+    int64_t n_near_tiles;          /* tiles whose distributions may take the FP64 near path */
     int64_t device_bytes;          /* device memory held by the context */
     int32_t precision;
     int32_t tile_size;

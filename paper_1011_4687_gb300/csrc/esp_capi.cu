@@ -570,6 +570,7 @@ esp_status esp_get_info(const esp_ctx *ctx, esp_info *info)
     for (int l = 0; l <= kMaxL; ++l)
         info->n_by_L[l] = ctx->env.n_by_L[l];
     info->n_tiles = ctx->n_tiles;
+    info->n_near_tiles = ctx->env.n_near_tiles;
     info->device_bytes = ctx->device_bytes;
     info->precision = ctx->opt.precision;
     info->tile_size = ctx->env.tile_size;
@@ -696,3 +697,4 @@ esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int6
 }
 
 } // extern "C"
+

@@ -10,7 +10,7 @@
 namespace esp {
 
 #ifndef ESP_SUM_BLOCK
-#define ESP_SUM_BLOCK 16
+#define ESP_SUM_BLOCK 4
 #endif
 // distributions summed in plain FP32 before a TwoSum into the running pair
 constexpr int kSumBlock = ESP_SUM_BLOCK;
@@ -156,14 +156,16 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
                     boys_far<L, float>(dx * dx + dy * dy + dz * dz, F);
                     v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
                 } else if constexpr (L == 0) {
-                    float T = ps * (dx * dx + dy * dy + dz * dz);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    float T = esp_fma(ps, r2, r[rec32_pslo(L)] * r2);
                     if constexpr (SHORT)
                         F[0] = boys_f0_short<float>(T);
                     else
                         boys_eval<L, float>(T, s_boys, F);
                     v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
                 } else {
-                    float x = ps * dx, y = ps * dy, z = ps * dz;
+                    const float pslo = r[rec32_pslo(L)];
+                    float x = esp_fma(ps, dx, pslo * dx), y = esp_fma(ps, dy, pslo * dy), z = esp_fma(ps, dz, pslo * dz);
                     float T = x * x + y * y + z * z;
                     boys_eval<L, float>(T, s_boys, F);
                     if constexpr (SHORT)
@@ -180,13 +182,14 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
 }
 
 // Per-position classification of a tile: near (FP64 instead; only with a
-// positive near_r) and far (the asymptotic form is exact to FP32 for every
+// positive near_r and for tiles whose distributions can produce potentials
+// above kNearVmax) and far (the asymptotic form is exact to FP32 for every
 // distribution of the tile).
 ESP_HD void classify_tile(const TileMeta &m, float cx, float cy, float cz, float near_r, bool &nearq, bool &farq)
 {
     float ex = cx - m.cx, ey = cy - m.cy, ez = cz - m.cz;
     float d = sqrtf(ex * ex + ey * ey + ez * ez) - m.rad;
-    nearq = near_r > 0.0f && d < near_r;
+    nearq = near_r > 0.0f && m.vmax >= kNearVmax && d < near_r;
     farq = nearq || (d > 0.0f && m.pmin * d * d >= kBoys32Tmax);
 }
 

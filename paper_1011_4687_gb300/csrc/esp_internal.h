@@ -28,9 +28,12 @@ namespace esp {
 
 constexpr int kMaxL = 4;
 constexpr int kClassPoint = 5;          // tile class of point charges
-// FP64 re-evaluation radius of the FP32C kernel when the caller leaves it unset:
-// off, since nuclei and on-site monopoles are FP64 point charges already.
-constexpr double kDefaultNearRadius = 0.0;
+// FP64 re-evaluation radius of the FP32C kernel when the caller leaves it unset.
+// It applies only to tiles holding a distribution whose potential can exceed
+// kNearVmax (|Q| 2 sqrt(p/pi) bounds the potential of a charge Q spread with
+// exponent p); nuclei and on-site monopoles are FP64 point charges already.
+constexpr double kDefaultNearRadius = 1.5;
+constexpr float kNearVmax = 2.0f;
 // Tile class bit: the distributions are centred on a point charge whose FP64
 // charge already includes their monopoles, so the tile holds only the
 // short-range remainder V_d - Q_d/|P - C| (Q_d = (pi/p)^{3/2} D_000).
@@ -42,13 +45,15 @@ ESP_HD constexpr int num_hermite(int L) { return (L + 1) * (L + 2) * (L + 3) / 6
 //   [4..7]          Px_lo, Py_lo, Pz_lo, M_0 lo word
 //   [8, 8+n)        M_tuv = (pi/p)^{3/2} D_tuv   (far-field multipole moments)
 //   [8+n]           G_0 lo word
-//   [9+n, 9+2n)     G_tuv                        (general form, see above)
+//   [9+n]           lo word of p (L = 0) or sqrt(p) (L > 0)
+//   [10+n, 10+2n)   G_tuv                        (general form, see above)
 // padded to a multiple of 4 floats.
 ESP_HD constexpr int rec32_lo(int) { return 4; }
 ESP_HD constexpr int rec32_m(int) { return 8; }
 ESP_HD constexpr int rec32_g0lo(int L) { return 8 + (L + 1) * (L + 2) * (L + 3) / 6; }
-ESP_HD constexpr int rec32_g(int L) { return 9 + (L + 1) * (L + 2) * (L + 3) / 6; }
-ESP_HD constexpr int rec32_stride(int L) { return ((9 + 2 * ((L + 1) * (L + 2) * (L + 3) / 6) + 3) / 4) * 4; }
+ESP_HD constexpr int rec32_pslo(int L) { return 9 + (L + 1) * (L + 2) * (L + 3) / 6; }
+ESP_HD constexpr int rec32_g(int L) { return 10 + (L + 1) * (L + 2) * (L + 3) / 6; }
+ESP_HD constexpr int rec32_stride(int L) { return ((10 + 2 * ((L + 1) * (L + 2) * (L + 3) / 6) + 3) / 4) * 4; }
 constexpr int kRec32MaxStride = 80;
 // FP64 record stride (doubles): [Px, Py, Pz, sqrt(p), G_0 .. G_{n-1}], padded to 2.
 ESP_HD constexpr int rec64_stride(int L) { return ((4 + (L == 0 ? 1 : L == 1 ? 4 : L == 2 ? 10 : L == 3 ? 20 : 35) + 1) / 2) * 2; }
@@ -61,7 +66,8 @@ constexpr float kBoysInvStep = 8.0f;
 constexpr int kBoys32Terms = 6;          // Taylor terms (k = 0..5) of the FP32 table
 constexpr float kBoys32Tmax = 30.0f;     // asymptotic form at and above this T
 constexpr int kBoys32Rows = 241;         // T_i up to 30
-constexpr int kBoys32Row = 12;           // F_0..F_9, exp(-T_i), pad
+constexpr int kBoys32Row = 20;           // F_0..F_9, exp(-T_i), pad, lo words of F_0..F_4 and exp, pad
+constexpr int kBoys32LoCol = 12;         // low words: F_n at kBoys32LoCol + n (n <= 4), exp at + 5
 constexpr int kBoys64Terms = 9;          // Taylor terms (k = 0..8) of the FP64 table
 constexpr double kBoys64Tmax = 45.0;
 constexpr int kBoys64Rows = 361;         // T_i up to 45
@@ -76,7 +82,8 @@ struct TileMeta {
     float rad;        // bounding-sphere radius
     float pmin;       // smallest exponent p in the tile (0 for point tiles)
     float qabs;       // sum of absolute charge bounds of the tile's entries
-    float pad0, pad1;
+    float vmax;       // largest |Q_d| 2 sqrt(p_d/pi) of an unmerged distribution (0 if none)
+    float pad1;
 };
 static_assert(sizeof(TileMeta) == 48, "TileMeta layout");
 
@@ -166,16 +173,25 @@ ESP_HD void boys_eval(R T, const R *__restrict__ tab, R (&F)[L + 1])
         R md = -d;
         R f = row[L + C::kTerms - 1];
 #pragma unroll
-        for (int k = C::kTerms - 2; k >= 0; --k)
+        for (int k = C::kTerms - 2; k >= 1; --k)
             f = f * (md * R(1.0 / (k + 1))) + row[L + k];
-        F[L] = f;
+        f = f * md; // sum_{k>=1} F_{L+k}(T_i) (-d)^k / k!
+        if constexpr (sizeof(R) == 4)
+            F[L] = row[L] + (row[kBoys32LoCol + L] + f); // leading value carries a low word
+        else
+            F[L] = row[L] + f;
         if constexpr (L > 0) {
-            // exp(-T) = exp(-T_i) * exp(-d), exp(-d) by its Taylor series (|d| <= 1/16)
-            R e = R(1);
+            // exp(-T) = exp(-T_i) * exp(-d), exp(-d) - 1 by its Taylor series (|d| <= 1/16)
+            R q = R(1);
 #pragma unroll
-            for (int k = C::kTerms; k >= 1; --k)
-                e = e * (md * R(1.0 / k)) + R(1);
-            e *= row[C::kExpCol];
+            for (int k = C::kTerms; k >= 2; --k)
+                q = q * (md * R(1.0 / k)) + R(1);
+            q = q * md;
+            R e;
+            if constexpr (sizeof(R) == 4)
+                e = row[C::kExpCol] + esp_fma(row[C::kExpCol], q, row[kBoys32LoCol + 5]);
+            else
+                e = row[C::kExpCol] + row[C::kExpCol] * q;
             R T2 = T + T;
 #pragma unroll
             for (int n = L - 1; n >= 0; --n)

@@ -94,7 +94,7 @@ void boys_by_quadrature(double T, int nmax, double *F)
 }
 
 template <typename R>
-std::vector<R> make_boys_table(int rows, int row_len, int nmax, int exp_col)
+std::vector<R> make_boys_table(int rows, int row_len, int nmax, int exp_col, int lo_col)
 {
     std::vector<R> tab(size_t(rows) * row_len, R(0));
     std::vector<double> F(nmax + 1);
@@ -104,6 +104,11 @@ std::vector<R> make_boys_table(int rows, int row_len, int nmax, int exp_col)
         for (int n = 0; n <= nmax; ++n)
             tab[size_t(i) * row_len + n] = R(F[n]);
         tab[size_t(i) * row_len + exp_col] = R(std::exp(-T));
+        if (lo_col > 0) {
+            for (int n = 0; n <= kMaxL; ++n)
+                tab[size_t(i) * row_len + lo_col + n] = R(F[n] - double(R(F[n])));
+            tab[size_t(i) * row_len + lo_col + kMaxL + 1] = R(std::exp(-T) - double(R(std::exp(-T))));
+        }
     }
     return tab;
 }
@@ -257,7 +262,7 @@ const std::vector<float> &boys_table32()
     static std::once_flag once;
     std::call_once(once, [] {
         t = make_boys_table<float>(kBoys32Rows, kBoys32Row, kMaxL + kBoys32Terms - 1,
-                                   BoysConst<float>::kExpCol);
+                                   BoysConst<float>::kExpCol, kBoys32LoCol);
     });
     return t;
 }
@@ -268,7 +273,7 @@ const std::vector<double> &boys_table64()
     static std::once_flag once;
     std::call_once(once, [] {
         t = make_boys_table<double>(kBoys64Rows, kBoys64Row, kMaxL + kBoys64Terms - 1,
-                                    BoysConst<double>::kExpCol);
+                                    BoysConst<double>::kExpCol, 0);
     });
     return t;
 }
@@ -574,7 +579,7 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         m.n = int32_t(e - s);
         m.off32 = int32_t(off32);
         m.off64 = int32_t(off64);
-        double pmin = 1e300, qsum = 0.0;
+        double pmin = 1e300, qsum = 0.0, vmax = 0.0;
         cbuf.clear();
         for (size_t k = s; k < e; ++k) {
             const Dist &d = dist[k];
@@ -582,12 +587,16 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
                 cbuf.push_back(d.P[c]);
             pmin = std::min(pmin, d.p);
             qsum += d.qabs;
+            if (!shortr)
+                vmax = std::max(vmax, std::fabs(d.M[0]) * 2.0 * std::sqrt(d.p / kPi));
             out.n_by_L[L] += 1;
             size_t b32 = out.rec32.size();
             out.rec32.resize(b32 + st32, 0.0f);
             for (int c = 0; c < 3; ++c)
                 out.rec32[b32 + c] = float(quantize_hi(d.P[c], out.coord_quantum));
-            out.rec32[b32 + 3] = L == 0 ? float(d.p) : float(std::sqrt(d.p));
+            const double psv = L == 0 ? d.p : std::sqrt(d.p);
+            out.rec32[b32 + 3] = float(psv);
+            out.rec32[b32 + rec32_pslo(L)] = float(psv - double(float(psv)));
             for (int c = 0; c < 3; ++c)
                 out.rec32[b32 + rec32_lo(L) + c] = float(d.P[c] - quantize_hi(d.P[c], out.coord_quantum));
             out.rec32[b32 + rec32_lo(L) + 3] = shortr ? 0.0f : float(d.M[0] - double(float(d.M[0])));
@@ -610,6 +619,8 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         bounding_sphere(cbuf.data(), 3, m.n, m);
         m.pmin = float(pmin);
         m.qabs = float(qsum);
+        m.vmax = float(vmax);
+        out.n_near_tiles += vmax >= kNearVmax;
         out.tiles.push_back(m);
         s = e;
     }

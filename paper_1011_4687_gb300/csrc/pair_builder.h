@@ -19,6 +19,7 @@ struct HostEnv {
     int64_t n_distributions = 0;
     int64_t n_screened = 0;
     int64_t n_by_L[kMaxL + 1] = {0, 0, 0, 0, 0};
+    int64_t n_near_tiles = 0;      // tiles eligible for the FP64 near path
     int tile_size = 128;
     // Grid of the FP32 high words of coordinates (a power of two): centres and
     // positions are split as x = hi + lo with hi a multiple of coord_quantum, so

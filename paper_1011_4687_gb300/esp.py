@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("n_point_charges", ctypes.c_int64), ("n_pairs_in", ctypes.c_int64),
                 ("n_distributions", ctypes.c_int64), ("n_screened", ctypes.c_int64),
-                ("n_by_L", ctypes.c_int64 * 5), ("n_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("n_by_L", ctypes.c_int64 * 5), ("n_tiles", ctypes.c_int64), ("n_near_tiles", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("tile_size", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("positions_per_thread", ctypes.c_int32),
                 ("pair_splits", ctypes.c_int32), ("device", ctypes.c_int32)]

@@ -239,8 +239,9 @@ def test_onsite_monopoles_move_to_point_charges(lib):
     assert np.allclose(env.debug_host_eval(wl.positions), ref, rtol=1e-12, atol=1e-12)
     env32 = _host_env(wl, screen_tol=0.0, precision="fp32c")
     assert np.abs(env32.debug_host_eval(wl.positions) - ref).max() <= 2e-6
-    # a position at 1e-3 bohr from a nucleus: the FP64 near path takes the atom
+    # a position 1e-3 bohr from a nucleus (|V| ~ 7e3): FP64 to 1e-12, FP32C to a
+    # few FP32 ulps relative (the short-range remainder is large there)
     C = wl.nuclei_xyz[3] + np.array([1e-3, 0.0, 0.0])
     r1 = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, C[None])
     assert np.allclose(env.debug_host_eval(C[None]), r1, rtol=1e-12)
-    assert np.allclose(env32.debug_host_eval(C[None]), r1, rtol=1e-10)
+    assert np.allclose(env32.debug_host_eval(C[None]), r1, rtol=2e-7)
