@@ -165,6 +165,32 @@ esp_status esp_eval(esp_ctx *ctx, const double *positions, int64_t n, double *V_
 esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_walkers,
                             int64_t n_elec, double *V_out, double *E_out);
 
+/* Largest n accepted by esp_eval_noalloc. */
+#define ESP_NOALLOC_MAX_POSITIONS 65536
+
+/* esp_eval without any device allocation (the paper has no counterpart; this
+ * entry point exists for callers of this library that cannot call cudaMalloc:
+ * code whose device memory is owned by another allocator, such as a
+ * framework's caching allocator that already holds the GPU, and Monte Carlo
+ * loops that must not pay cudaMalloc's implicit device-wide synchronisation).
+ * The context must have been created beforehand by esp_create.
+ *   positions [n][3] device memory of the context's device, float64
+ *   V_out     [n]    device memory of the context's device, float64
+ * Work is enqueued on the context's stream; the call returns without waiting.
+ * The scratch (staged positions and per-split partial sums) lives in one
+ * file-scope device array of fixed size inside the library, about 7 MiB for
+ * ESP_NOALLOC_MAX_POSITIONS positions, which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other contexts, other threads) race on it, so order them on one
+ * stream or synchronise between them.  The result equals esp_eval's within
+ * FP32C rounding (the per-split partial count is capped at 8 here).
+ * Errors: ESP_ERR_INVALID (n > ESP_NOALLOC_MAX_POSITIONS, host pointers, null
+ * pointers), ESP_ERR_STATE, ESP_ERR_CUDA.  Calls no cudaMalloc or cudaFree. */
+esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, int64_t n, double *V_out);
+
 /* Switch the arithmetic of later evaluations (ESP_FP64 or ESP_FP32C). */
 esp_status esp_set_precision(esp_ctx *ctx, int32_t precision);
 

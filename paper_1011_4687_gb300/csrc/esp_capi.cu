@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -698,3 +699,115 @@ esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int6
 
 } // extern "C"
 
+// ---------------------------------------------------------------------------
+// esp_eval_noalloc: the same pipeline with its scratch in a fixed device array
+// instead of context-owned cudaMalloc buffers.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoallocMaxPositions = ESP_NOALLOC_MAX_POSITIONS;
+constexpr int kNoallocMaxSplits = 8;
+constexpr size_t kNoallocStageBytes = size_t(kNoallocMaxPositions) * (3 * sizeof(double) + 6 * sizeof(float));
+constexpr size_t kNoallocBytes = kNoallocStageBytes + size_t(kNoallocMaxPositions) * kNoallocMaxSplits * sizeof(double);
+constexpr int kNoallocMaxDevices = 64;
+
+} // namespace
+
+// Scratch of esp_eval_noalloc: staged positions, then per-split partial sums.
+// Host code must not pass this symbol to a kernel; it uses the device address
+// obtained by cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` (which must be current);
+// looked up once per device.
+esp_status noalloc_scratch(int device, void **out)
+{
+    if (device < 0 || device >= kNoallocMaxDevices)
+        return fail(ESP_ERR_UNSUPPORTED, "device ordinal %d beyond the no-allocation table", device);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "locating the no-allocation scratch");
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return ESP_OK;
+}
+
+} // namespace
+
+extern "C" esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, int64_t n, double *V_out)
+{
+    g_last_error.clear();
+    if (!valid_ctx(ctx) || ctx->device < 0)
+        return fail(ESP_ERR_STATE, "invalid or host-only context");
+    if (n < 0 || n > kNoallocMaxPositions)
+        return fail(ESP_ERR_INVALID, "n = %lld outside [0, %lld] for esp_eval_noalloc", (long long)n,
+                    (long long)kNoallocMaxPositions);
+    if (n == 0)
+        return ESP_OK;
+    if (!positions || !V_out)
+        return fail(ESP_ERR_INVALID, "null positions or V_out");
+    BusyGuard busy(ctx->busy);
+    if (!busy.acquired)
+        return fail(ESP_ERR_STATE, "context is in use by another thread");
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok)
+        return fail(ESP_ERR_CUDA, "cannot select device %d", ctx->device);
+    if (classify(positions, ctx->device) != Space::Device || classify(V_out, ctx->device) != Space::Device)
+        return fail(ESP_ERR_INVALID, "esp_eval_noalloc takes device memory of device %d only", ctx->device);
+    void *base = nullptr;
+    esp_status st = noalloc_scratch(ctx->device, &base);
+    if (st != ESP_OK)
+        return st;
+    const int prec = ctx->opt.precision == ESP_FP64 ? 0 : 1;
+    const int splits = std::min(choose_splits(ctx, int(n), prec), kNoallocMaxSplits);
+    char *b = static_cast<char *>(base);
+    Staged stg;
+    stg.x64 = reinterpret_cast<double *>(b);
+    stg.y64 = stg.x64 + n;
+    stg.z64 = stg.y64 + n;
+    float *f = reinterpret_cast<float *>(stg.z64 + n);
+    stg.xh = f;
+    stg.yh = f + n;
+    stg.zh = f + 2 * n;
+    stg.xl = f + 3 * n;
+    stg.yl = f + 4 * n;
+    stg.zl = f + 5 * n;
+    double *partial = reinterpret_cast<double *>(b + kNoallocStageBytes);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    if ((e = launch_stage(positions, int(n), ctx->opt.qm_center, ctx->env.coord_quantum, stg, s)) != cudaSuccess)
+        return cuda_fail(e, "staging positions");
+    if (ctx->n_tiles == 0) {
+        // nothing writes the partial sums: they must start at zero
+        if ((e = cudaMemsetAsync(partial, 0, size_t(n) * splits * sizeof(double), s)) != cudaSuccess)
+            return cuda_fail(e, "clearing partial sums");
+    } else {
+        EvalArgs a;
+        a.n_pos = int(n);
+        a.n_splits = splits;
+        a.n_tiles = ctx->n_tiles;
+        a.tile_size = ctx->env.tile_size;
+        a.pos = stg;
+        a.tiles = static_cast<const TileMeta *>(ctx->tiles.p);
+        a.rec32 = static_cast<const float *>(ctx->rec32.p);
+        a.rec64 = static_cast<const double *>(ctx->rec64.p);
+        a.boys32 = static_cast<const float *>(ctx->boys32.p);
+        a.boys64 = static_cast<const double *>(ctx->boys64.p);
+        a.partial = partial;
+        a.near_r = float(ctx->opt.near_radius < 0.0 ? kDefaultNearRadius : ctx->opt.near_radius);
+        if ((e = launch_potential(prec, a, ctx->threads[prec], ctx->ppt[prec], s)) != cudaSuccess)
+            return cuda_fail(e, "launching the potential kernel");
+    }
+    if ((e = launch_reduce(partial, splits, int(n), V_out, s)) != cudaSuccess)
+        return cuda_fail(e, "launching the partial-sum reduction");
+    return ESP_OK;
+}
