@@ -124,15 +124,16 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("esp_kernels.cu", "esp_internal.h"):
+    for name in ("esp_kernels.cu", "esp_internal.h", "esp_eval_core.h"):
         with open(os.path.join(ROOT, "paper_1011_4687_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, units: float):
-    """DRAM bytes per launch from the committed ncu summary, scaled to `units`
-    (positions x evals) — None if the kernel source changed since the capture."""
+def profiled_traffic(kernel: str, n_pos: int):
+    """DRAM bytes of one launch at n_pos positions, from the committed ncu
+    counters: bytes for the environment (read once, L2-resident) plus bytes per
+    position; None if the kernel source changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -141,7 +142,7 @@ def profiled_traffic(kernel: str, units: float):
     e = t.get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e["dram_bytes_per_launch"] * units / e["units_per_launch"]
+    return e["fixed_bytes"] + e["bytes_per_position"] * n_pos
 
 
 def build_workload(rank: int, walkers: int = 4096):
@@ -318,7 +319,7 @@ def main(argv=None):
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6
     ops_launch = n_pos * sum(OPS_PER_EVAL[L] * info["n_by_L"][L] for L in range(5))
     achieved = ops_launch / (kern * 1e-3)
-    traffic = profiled_traffic("potential_f32c_kernel", float(evals_per_step))
+    traffic = profiled_traffic("potential_f32c_kernel", n_pos)
 
     out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
