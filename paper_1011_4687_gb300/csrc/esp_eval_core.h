@@ -139,12 +139,30 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
         const int j1 = (j0 + kSumBlock < n) ? j0 + kSumBlock : n;
         for (int j = j0; j < j1; ++j) {
             const float *r = s_rec + j * st;
-            const float px = r[0], py = r[1], pz = r[2], ps = r[3];
-            const float plx = r[lo], ply = r[lo + 1], plz = r[lo + 2], k0lo = r[c0lo];
+            const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
+            const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
+            const float px = r0.x, py = r0.y, pz = r0.z, ps = r0.w;
+            const float plx = r1.x, ply = r1.y, plz = r1.z;
+            const float k0lo = FAR ? r1.w : r[c0lo];
             float K[nh];
+            if constexpr (FAR) {
+                // the moments start 16-byte aligned: whole float4 loads
 #pragma unroll
-            for (int h = 0; h < nh; ++h)
-                K[h] = r[co + h];
+                for (int h = 0; h + 3 < nh; h += 4) {
+                    const float4 k4 = reinterpret_cast<const float4 *>(r + co)[h / 4];
+                    K[h] = k4.x;
+                    K[h + 1] = k4.y;
+                    K[h + 2] = k4.z;
+                    K[h + 3] = k4.w;
+                }
+#pragma unroll
+                for (int h = nh - nh % 4; h < nh; ++h)
+                    K[h] = r[co + h];
+            } else {
+#pragma unroll
+                for (int h = 0; h < nh; ++h)
+                    K[h] = r[co + h];
+            }
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
                 float dx = (px - ch[q][0]) + (plx - cl[q][0]);

@@ -299,7 +299,7 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         err = "bad options (qm_center or screen_tol)";
         return ESP_ERR_INVALID;
     }
-    int tile = opt.tile_size == 0 ? 128 : opt.tile_size;
+    int tile = opt.tile_size == 0 ? 64 : opt.tile_size;
     if (tile != 64 && tile != 128 && tile != 256) {
         err = "tile_size must be 64, 128 or 256";
         return ESP_ERR_INVALID;

@@ -20,7 +20,7 @@ struct HostEnv {
     int64_t n_screened = 0;
     int64_t n_by_L[kMaxL + 1] = {0, 0, 0, 0, 0};
     int64_t n_near_tiles = 0;      // tiles eligible for the FP64 near path
-    int tile_size = 128;
+    int tile_size = 64;
     // Grid of the FP32 high words of coordinates (a power of two): centres and
     // positions are split as x = hi + lo with hi a multiple of coord_quantum, so
     // P_hi - C_hi is exact in FP32 whenever |P_hi - C_hi| < 2^24 * coord_quantum.
