@@ -191,6 +191,58 @@ esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_wal
  * pointers), ESP_ERR_STATE, ESP_ERR_CUDA.  Calls no cudaMalloc or cudaFree. */
 esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, int64_t n, double *V_out);
 
+/* ------------------------------------------------------------------------
+ * Batched evaluation of many independent systems (environment, positions).
+ * An FMO calculation has many fragments and fragment pairs (Eq. FMO), each
+ * with its own environment field, and QMC runs many walkers: the batch
+ * evaluates all systems together with one persistent potential kernel that
+ * takes (system, position block, pair split) work items, largest first, and
+ * replays one captured CUDA graph per call.
+ * ------------------------------------------------------------------------ */
+typedef struct esp_batch esp_batch;
+
+typedef struct {
+    int32_t threads_per_block;    /* chosen launch shape */
+    int32_t positions_per_thread;
+    double split_scale;           /* chosen multiplier of the per-system split count */
+    double best_ms;               /* time of one batched evaluation with that choice */
+    int32_t n_tried;              /* candidates timed (<= 16) */
+    int32_t tried_threads[16];
+    int32_t tried_ppt[16];
+    double tried_scale[16];
+    double tried_ms[16];
+} esp_tune_report;
+
+/* Batch of n_sys existing contexts (kept by pointer: they must outlive the
+ * batch).  All contexts must be on one device and use one precision.  Work
+ * runs on cuda_stream (NULL = default stream).  Errors: ESP_ERR_INVALID,
+ * ESP_ERR_STATE (host-only or invalid context), ESP_ERR_OOM, ESP_ERR_CUDA. */
+esp_status esp_batch_create(esp_ctx *const *ctxs, int32_t n_sys, void *cuda_stream, esp_batch **out);
+
+/* V_out[s][i] = potential of system s at positions[s][i].
+ *   positions [n_sys] host array of device pointers, each [n[s]][3] float64
+ *   n         [n_sys] host array of counts (0 allowed)
+ *   V_out     [n_sys] host array of device pointers, each [n[s]] float64
+ * Enqueued on the batch's stream; returns without waiting.  Scratch grows on
+ * demand.  Errors: ESP_ERR_INVALID (host memory, bad counts), ESP_ERR_STATE,
+ * ESP_ERR_OOM, ESP_ERR_CUDA. */
+esp_status esp_batch_eval(esp_batch *b, const double *const *positions, const int64_t *n, double *const *V_out);
+
+/* Time every built launch shape with split multipliers 0.5, 1 and 2 on the
+ * given inputs (outputs are overwritten), keep the fastest and report all. */
+esp_status esp_batch_autotune(esp_batch *b, const double *const *positions, const int64_t *n, double *const *V_out,
+                              esp_tune_report *report);
+
+/* Set the launch shape (FP32C: 128x4, 128x2, 256x2, 64x4; FP64: 128x2, 128x1,
+ * 256x1) and split multiplier directly. */
+esp_status esp_batch_set_shape(esp_batch *b, int32_t threads, int32_t ppt, double split_scale);
+
+/* Wait for the last batched evaluation and return its device time (ms). */
+esp_status esp_batch_last_ms(esp_batch *b, double *ms);
+
+/* Free the batch (not its contexts).  NULL is a no-op. */
+void esp_batch_destroy(esp_batch *b);
+
 /* Switch the arithmetic of later evaluations (ESP_FP64 or ESP_FP32C). */
 esp_status esp_set_precision(esp_ctx *ctx, int32_t precision);
 

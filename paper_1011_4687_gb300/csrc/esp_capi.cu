@@ -18,132 +18,22 @@
 #include <cuda_runtime.h>
 
 #include "../../include/esp.h"
+#include "esp_ctx.h"
 #include "esp_eval_core.h"
-#include "esp_kernels.h"
-#include "pair_builder.h"
 
 using namespace esp;
 
+std::string &esp::last_error()
+{
+    static thread_local std::string msg;
+    return msg;
+}
+
 namespace {
-
-thread_local std::string g_last_error;
-
-esp_status fail(esp_status s, const char *fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
-    va_end(ap);
-    g_last_error = buf;
-    return s;
-}
-
-esp_status cuda_fail(cudaError_t e, const char *what)
-{
-    if (e == cudaErrorMemoryAllocation)
-        return fail(ESP_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
-    return fail(ESP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    void release()
-    {
-        if (p)
-            cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    cudaError_t ensure(size_t need)
-    {
-        if (need <= bytes)
-            return cudaSuccess;
-        release();
-        cudaError_t e = cudaMalloc(&p, need);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            return e;
-        }
-        bytes = need;
-        return cudaSuccess;
-    }
-};
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess)
-            ok = true;
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0)
-            cudaSetDevice(prev);
-    }
-};
-
-struct BusyGuard {
-    std::atomic<int> &flag;
-    bool acquired;
-    explicit BusyGuard(std::atomic<int> &f) : flag(f)
-    {
-        int expect = 0;
-        acquired = flag.compare_exchange_strong(expect, 1);
-    }
-    ~BusyGuard()
-    {
-        if (acquired)
-            flag.store(0);
-    }
-};
 
 } // namespace
 
-struct esp_ctx {
-    int device = 0;
-    int num_sms = 152;
-    cudaStream_t stream = nullptr;
-    esp_options opt;
-    HostEnv env;             // host copy of the tiles (kept for esp_get_info / test hook)
-    bool host_copy = true;
-    DevBuf tiles, rec32, rec64, boys32, boys64;
-    DevBuf in, stage, partial, vout, eout;
-    std::atomic<int> busy{0};
-    int64_t device_bytes = 0;
-    int n_tiles = 0;
-    int threads[2] = {128, 128};  // per precision (0 = FP64, 1 = FP32C)
-    int ppt[2] = {2, 4};
-    bool timing = false;
-    bool timed_valid = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr}; // pipeline start, kernel start/end, pipeline end
-    uint32_t magic = 0x45535021u;
-};
-
-namespace {
-
-bool valid_ctx(const esp_ctx *c) { return c && c->magic == 0x45535021u; }
-
-enum class Space { Host, Device, Invalid };
-
-Space classify(const void *p, int device)
-{
-    cudaPointerAttributes at;
-    cudaError_t e = cudaPointerGetAttributes(&at, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return Space::Host;
-    }
-    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
-        return at.device == device ? Space::Device : Space::Invalid;
-    return Space::Host;
-}
-
-int choose_splits(const esp_ctx *c, int n, int prec)
+int esp::choose_splits(const esp_ctx *c, int n, int prec)
 {
     if (c->opt.pair_splits > 0)
         return std::max(1, std::min(c->opt.pair_splits, std::max(c->n_tiles, 1)));
@@ -157,6 +47,8 @@ int choose_splits(const esp_ctx *c, int n, int prec)
     s = std::min(s, 64);
     return std::max(s, 1);
 }
+
+namespace {
 
 esp_status ensure_scratch(esp_ctx *c, int64_t n, int splits, bool host_io, int64_t n_walkers)
 {
@@ -401,7 +293,7 @@ void esp_default_options(esp_options *opt)
 
 int32_t esp_abi_version(void) { return ESP_ABI_VERSION; }
 
-const char *esp_last_error(void) { return g_last_error.c_str(); }
+const char *esp_last_error(void) { return last_error().c_str(); }
 
 const char *esp_status_string(esp_status s)
 {
@@ -420,7 +312,7 @@ const char *esp_status_string(esp_status s)
 esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const esp_gauss_pair *pairs,
                       const double *weights, int64_t n_pairs, const esp_options *opt_in, esp_ctx **out)
 {
-    g_last_error.clear();
+    last_error().clear();
     if (!out)
         return fail(ESP_ERR_INVALID, "out is NULL");
     esp_options opt;
@@ -512,7 +404,7 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const 
 
 esp_status esp_eval(esp_ctx *ctx, const double *positions, int64_t n, double *V_out)
 {
-    g_last_error.clear();
+    last_error().clear();
     if (!valid_ctx(ctx) || ctx->device < 0)
         return fail(ESP_ERR_STATE, "invalid or host-only context");
     if (n > 0 && !V_out)
@@ -523,7 +415,7 @@ esp_status esp_eval(esp_ctx *ctx, const double *positions, int64_t n, double *V_
 esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_walkers, int64_t n_elec,
                             double *V_out, double *E_out)
 {
-    g_last_error.clear();
+    last_error().clear();
     if (!valid_ctx(ctx) || ctx->device < 0)
         return fail(ESP_ERR_STATE, "invalid or host-only context");
     if (n_walkers < 0 || n_elec < 0 || n_walkers > (int64_t(1) << 30) || n_elec > (int64_t(1) << 20))
@@ -747,7 +639,7 @@ esp_status noalloc_scratch(int device, void **out)
 
 extern "C" esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, int64_t n, double *V_out)
 {
-    g_last_error.clear();
+    last_error().clear();
     if (!valid_ctx(ctx) || ctx->device < 0)
         return fail(ESP_ERR_STATE, "invalid or host-only context");
     if (n < 0 || n > kNoallocMaxPositions)

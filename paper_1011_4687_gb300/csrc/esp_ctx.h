@@ -1,0 +1,137 @@
+// Context internals shared by the C-ABI translation units.
+#pragma once
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/esp.h"
+#include "esp_kernels.h"
+#include "pair_builder.h"
+
+namespace esp {
+
+// message of the last failing call in this thread (esp_last_error)
+std::string &last_error();
+
+inline esp_status fail(esp_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    last_error() = buf;
+    return s;
+}
+
+inline esp_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(ESP_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(ESP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release()
+    {
+        if (p)
+            cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t need)
+    {
+        if (need <= bytes)
+            return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = need;
+        return cudaSuccess;
+    }
+};
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess)
+            ok = true;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+struct BusyGuard {
+    std::atomic<int> &flag;
+    bool acquired;
+    explicit BusyGuard(std::atomic<int> &f) : flag(f)
+    {
+        int expect = 0;
+        acquired = flag.compare_exchange_strong(expect, 1);
+    }
+    ~BusyGuard()
+    {
+        if (acquired)
+            flag.store(0);
+    }
+};
+
+enum class Space { Host, Device, Invalid };
+
+inline Space classify(const void *p, int device)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return Space::Host;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return at.device == device ? Space::Device : Space::Invalid;
+    return Space::Host;
+}
+
+} // namespace esp
+
+struct esp_ctx {
+    int device = 0;
+    int num_sms = 152;
+    cudaStream_t stream = nullptr;
+    esp_options opt;
+    esp::HostEnv env;        // host copy of the tiles (kept for esp_get_info / test hook)
+    bool host_copy = true;
+    esp::DevBuf tiles, rec32, rec64, boys32, boys64;
+    esp::DevBuf in, stage, partial, vout, eout;
+    std::atomic<int> busy{0};
+    int64_t device_bytes = 0;
+    int n_tiles = 0;
+    int threads[2] = {128, 128};  // per precision (0 = FP64, 1 = FP32C)
+    int ppt[2] = {2, 4};
+    bool timing = false;
+    bool timed_valid = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr}; // pipeline start, kernel start/end, pipeline end
+    uint32_t magic = 0x45535021u;
+};
+
+namespace esp {
+inline bool valid_ctx(const esp_ctx *c) { return c && c->magic == 0x45535021u; }
+// per-split count for n positions in precision prec (0 FP64, 1 FP32C)
+int choose_splits(const esp_ctx *c, int n, int prec);
+} // namespace esp

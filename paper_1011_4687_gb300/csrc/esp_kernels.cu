@@ -14,6 +14,8 @@
 #include "esp_eval_core.h"
 #include "esp_kernels.h"
 
+#include <algorithm>
+
 namespace esp {
 
 namespace {
@@ -50,17 +52,14 @@ __device__ __forceinline__ void copy_tile(float4 *__restrict__ dst, const float4
 // ---------------------------------------------------------------------------
 // FP32C kernel
 // ---------------------------------------------------------------------------
+// One CTA's work in the FP32C kernel: position block bx against the tiles of
+// split `split` (tiles split, split + n_splits, ...).  The Boys table is
+// already in shared memory (s_boys); s_tile4 holds one staged tile.
 template <int NT, int PPT>
-__global__ void __launch_bounds__(NT) potential_f32c_kernel(EvalArgs a)
+__device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, float4 *s_tile4,
+                                         const float *s_boys)
 {
-    extern __shared__ float4 smem4[];
-    float4 *s_tile4 = smem4;
-    float *s_boys = reinterpret_cast<float *>(smem4 + (a.tile_size * kRec32MaxStride) / 4);
-    for (int i = threadIdx.x; i < kBoys32Rows * kBoys32Row; i += NT)
-        s_boys[i] = a.boys32[i];
-
-    const int split = blockIdx.y;
-    const int base = blockIdx.x * NT * PPT + threadIdx.x;
+    const int base = bx * NT * PPT + threadIdx.x;
     float ch[PPT][3], cl[PPT][3];
     float S[PPT], Cc[PPT];
     double acc64[PPT];
@@ -151,6 +150,17 @@ __global__ void __launch_bounds__(NT) potential_f32c_kernel(EvalArgs a)
             a.partial[(size_t)split * a.n_pos + idx[q]] = ((double)S[q] + (double)Cc[q]) + acc64[q];
 }
 
+template <int NT, int PPT>
+__global__ void __launch_bounds__(NT) potential_f32c_kernel(EvalArgs a)
+{
+    extern __shared__ float4 smem4[];
+    float4 *s_tile4 = smem4;
+    float *s_boys = reinterpret_cast<float *>(smem4 + (a.tile_size * kRec32MaxStride) / 4);
+    for (int i = threadIdx.x; i < kBoys32Rows * kBoys32Row; i += NT)
+        s_boys[i] = a.boys32[i];
+    cta_f32c<NT, PPT>(a, blockIdx.x, blockIdx.y, s_tile4, s_boys);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 kernel
 // ---------------------------------------------------------------------------
@@ -168,12 +178,10 @@ __device__ __forceinline__ void tile_f64(const double *__restrict__ s_rec, int n
 }
 
 template <int NT, int PPT>
-__global__ void __launch_bounds__(NT) potential_f64_kernel(EvalArgs a)
+__device__ __forceinline__ void cta_f64(const EvalArgs &a, int bx, int split, float4 *smem4)
 {
-    extern __shared__ float4 smem4[];
     const double *s_rec = reinterpret_cast<const double *>(smem4);
-    const int split = blockIdx.y;
-    const int base = blockIdx.x * NT * PPT + threadIdx.x;
+    const int base = bx * NT * PPT + threadIdx.x;
     double c[PPT][3], S[PPT], Cc[PPT];
     int idx[PPT];
 #pragma unroll
@@ -222,6 +230,119 @@ __global__ void __launch_bounds__(NT) potential_f64_kernel(EvalArgs a)
     for (int q = 0; q < PPT; ++q)
         if (idx[q] < a.n_pos)
             a.partial[(size_t)split * a.n_pos + idx[q]] = S[q] + Cc[q];
+}
+
+template <int NT, int PPT>
+__global__ void __launch_bounds__(NT) potential_f64_kernel(EvalArgs a)
+{
+    extern __shared__ float4 smem4[];
+    cta_f64<NT, PPT>(a, blockIdx.x, blockIdx.y, smem4);
+}
+
+// ---------------------------------------------------------------------------
+// Batched systems: persistent kernel over (system, position block, split)
+// work items taken from an atomic counter, plus grid-stride staging and
+// reduction over every system's positions.  All sizes and pointers come from
+// the device-side table (BatchHeader + SysDesc[]), so one captured CUDA graph
+// serves every call whose work fits the allocated capacity.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_sys(const SysDesc *__restrict__ sys, int n_sys, int key, bool by_item)
+{
+    int lo = 0, hi = n_sys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int v = by_item ? sys[mid].item_begin : sys[mid].pos_begin;
+        if (v <= key)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ EvalArgs args_of(const SysDesc &d, const float *boys32, const double *boys64)
+{
+    EvalArgs a;
+    a.n_pos = d.n_pos;
+    a.n_splits = d.splits;
+    a.n_tiles = d.n_tiles;
+    a.tile_size = d.tile_size;
+    a.pos = d.st;
+    a.tiles = d.tiles;
+    a.rec32 = d.rec32;
+    a.rec64 = d.rec64;
+    a.boys32 = boys32;
+    a.boys64 = boys64;
+    a.partial = d.partial;
+    a.near_r = d.near_r;
+    return a;
+}
+
+template <int NT, int PPT, int PREC>
+__global__ void __launch_bounds__(NT) batch_potential_kernel(const BatchHeader *__restrict__ hdr,
+                                                             const SysDesc *__restrict__ sys, int *counter,
+                                                             const float *boys32, const double *boys64,
+                                                             int tile_cap)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ int s_item;
+    float *s_boys = reinterpret_cast<float *>(smem4 + (tile_cap * kRec32MaxStride) / 4);
+    if (PREC == 1)
+        for (int i = threadIdx.x; i < kBoys32Rows * kBoys32Row; i += NT)
+            s_boys[i] = boys32[i];
+    const int n_items = hdr->n_items, n_sys = hdr->n_sys;
+    for (;;) {
+        __syncthreads(); // s_item and the tile buffer are free again
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items)
+            break;
+        const int k = find_sys(sys, n_sys, item, true);
+        const SysDesc &d = sys[k];
+        const int local = item - d.item_begin;
+        const EvalArgs a = args_of(d, boys32, boys64);
+        if (PREC == 1)
+            cta_f32c<NT, PPT>(a, local / d.splits, local % d.splits, smem4, s_boys);
+        else
+            cta_f64<NT, PPT>(a, local / d.splits, local % d.splits, smem4);
+    }
+}
+
+__global__ void batch_stage_kernel(const BatchHeader *__restrict__ hdr, const SysDesc *__restrict__ sys)
+{
+    const int total = hdr->n_pos_total, n_sys = hdr->n_sys;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        const SysDesc &d = sys[find_sys(sys, n_sys, g, false)];
+        const int i = g - d.pos_begin;
+        double x = d.pos_in[3 * i] - d.qm[0], y = d.pos_in[3 * i + 1] - d.qm[1], z = d.pos_in[3 * i + 2] - d.qm[2];
+        d.st.x64[i] = x;
+        d.st.y64[i] = y;
+        d.st.z64[i] = z;
+        const double q = d.quantum;
+        double xh = nearbyint(x / q) * q, yh = nearbyint(y / q) * q, zh = nearbyint(z / q) * q;
+        d.st.xh[i] = (float)xh;
+        d.st.yh[i] = (float)yh;
+        d.st.zh[i] = (float)zh;
+        d.st.xl[i] = (float)(x - xh);
+        d.st.yl[i] = (float)(y - yh);
+        d.st.zl[i] = (float)(z - zh);
+    }
+}
+
+__global__ void batch_reduce_kernel(const BatchHeader *__restrict__ hdr, const SysDesc *__restrict__ sys)
+{
+    const int total = hdr->n_pos_total, n_sys = hdr->n_sys;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        const SysDesc &d = sys[find_sys(sys, n_sys, g, false)];
+        const int i = g - d.pos_begin;
+        double s = 0.0, c = 0.0;
+        if (d.n_tiles > 0)
+            for (int k = 0; k < d.splits; ++k)
+                two_sum_acc(s, c, d.partial[(size_t)k * d.n_pos + i]);
+        d.V_out[i] = s + c;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -316,6 +437,53 @@ cudaError_t launch_potential(int precision, const EvalArgs &a, int threads, int 
     }
 #undef ESP_LAUNCH
     return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_batch(int precision, const BatchHeader *hdr, const SysDesc *sys, int *counter, int max_items,
+                         const float *boys32, const double *boys64, int tile_cap, int threads, int ppt,
+                         int num_sms, int max_pos_total, cudaStream_t s)
+{
+    const int sgrid = std::max(1, std::min(4 * num_sms, (max_pos_total + 255) / 256));
+    batch_stage_kernel<<<sgrid, 256, 0, s>>>(hdr, sys);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const size_t smem = potential_smem_bytes(precision, tile_cap);
+    dim3 block(threads);
+#define ESP_BLAUNCH(NT, PPT, PR)                                                                              \
+    if (threads == NT && ppt == PPT && precision == PR) {                                                   \
+        auto k = batch_potential_kernel<NT, PPT, PR>;                                                       \
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) \
+            return e;                                                                                       \
+        int per_sm = 0;                                                                                     \
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem)) != cudaSuccess)        \
+            return e;                                                                                       \
+        int grid = std::max(1, std::min(per_sm * num_sms, max_items));                                      \
+        k<<<grid, block, smem, s>>>(hdr, sys, counter, boys32, boys64, tile_cap);                           \
+        launched = true;                                                                                    \
+    }
+    bool launched = false;
+    ESP_BLAUNCH(128, 4, 1)
+    ESP_BLAUNCH(128, 2, 1)
+    ESP_BLAUNCH(256, 2, 1)
+    ESP_BLAUNCH(64, 4, 1)
+    ESP_BLAUNCH(128, 2, 0)
+    ESP_BLAUNCH(128, 1, 0)
+    ESP_BLAUNCH(256, 1, 0)
+#undef ESP_BLAUNCH
+    if (!launched)
+        return cudaErrorInvalidConfiguration;
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    batch_reduce_kernel<<<sgrid, 256, 0, s>>>(hdr, sys);
+    return cudaGetLastError();
+}
+
+bool batch_shape_supported(int precision, int threads, int ppt)
+{
+    if (precision == 1)
+        return (threads == 128 && (ppt == 4 || ppt == 2)) || (threads == 256 && ppt == 2) || (threads == 64 && ppt == 4);
+    return (threads == 128 && (ppt == 2 || ppt == 1)) || (threads == 256 && ppt == 1);
 }
 
 cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s)

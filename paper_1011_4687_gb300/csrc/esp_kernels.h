@@ -30,6 +30,33 @@ struct EvalArgs {
     float near_r;     // FP32C: FP64 re-evaluation radius around a tile's bounding sphere
 };
 
+// One system of a batched evaluation (device-side table entry).
+struct SysDesc {
+    const TileMeta *tiles;
+    const float *rec32;
+    const double *rec64;
+    const double *pos_in; // [n_pos][3] device
+    double *V_out;        // [n_pos] device
+    double *partial;      // [splits][n_pos]
+    Staged st;
+    double qm[3];
+    double quantum;
+    int n_tiles, tile_size, n_pos, splits, blocks, item_begin, pos_begin;
+    float near_r;
+};
+
+struct BatchHeader {
+    int n_sys, n_items, n_pos_total, pad;
+};
+
+// Batched pipeline on stream s: staging, persistent potential kernel over all
+// (system, block, split) items, reduction into each system's V_out.  The
+// counter must be zero when the potential kernel starts.
+cudaError_t launch_batch(int precision, const BatchHeader *hdr, const SysDesc *sys, int *counter, int max_items,
+                         const float *boys32, const double *boys64, int tile_cap, int threads, int ppt,
+                         int num_sms, int max_pos_total, cudaStream_t s);
+bool batch_shape_supported(int precision, int threads, int ppt);
+
 cudaError_t launch_stage(const double *pos_in, int n, const double center[3], double quantum, const Staged &st,
                          cudaStream_t s);
 // precision: 0 = FP64, 1 = FP32C.  threads in {64, 128, 256}, ppt in {1, 2, 4}.

@@ -56,6 +56,20 @@ class Info(ctypes.Structure):
         return d
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("positions_per_thread", ctypes.c_int32),
+                ("split_scale", ctypes.c_double), ("best_ms", ctypes.c_double), ("n_tried", ctypes.c_int32),
+                ("tried_threads", ctypes.c_int32 * 16), ("tried_ppt", ctypes.c_int32 * 16),
+                ("tried_scale", ctypes.c_double * 16), ("tried_ms", ctypes.c_double * 16)]
+
+    def as_dict(self):
+        n = self.n_tried
+        return {"threads_per_block": self.threads_per_block, "positions_per_thread": self.positions_per_thread,
+                "split_scale": self.split_scale, "best_ms": self.best_ms,
+                "tried": [{"threads": self.tried_threads[i], "ppt": self.tried_ppt[i],
+                           "split_scale": self.tried_scale[i], "ms": self.tried_ms[i]} for i in range(n)]}
+
+
 EXPORTED = ["esp_default_options", "esp_create", "esp_eval", "esp_eval_walkers", "esp_set_precision",
             "esp_get_info", "esp_synchronize", "esp_destroy", "esp_status_string", "esp_last_error",
             "esp_abi_version", "esp_debug_boys", "esp_debug_host_eval", "esp_set_timing", "esp_last_timing"]
@@ -105,6 +119,19 @@ def load(build_if_missing: bool = False):
     lib.esp_debug_boys.restype = ctypes.c_int
     lib.esp_debug_host_eval.argtypes = [P, P, i64, P]
     lib.esp_debug_host_eval.restype = ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.esp_batch_create.argtypes = [PP, i32, P, ctypes.POINTER(P)]
+    lib.esp_batch_create.restype = ctypes.c_int
+    lib.esp_batch_eval.argtypes = [P, PP, ctypes.POINTER(i64), PP]
+    lib.esp_batch_eval.restype = ctypes.c_int
+    lib.esp_batch_autotune.argtypes = [P, PP, ctypes.POINTER(i64), PP, ctypes.POINTER(TuneReport)]
+    lib.esp_batch_autotune.restype = ctypes.c_int
+    lib.esp_batch_set_shape.argtypes = [P, i32, i32, d]
+    lib.esp_batch_set_shape.restype = ctypes.c_int
+    lib.esp_batch_last_ms.argtypes = [P, ctypes.POINTER(d)]
+    lib.esp_batch_last_ms.restype = ctypes.c_int
+    lib.esp_batch_destroy.argtypes = [P]
+    lib.esp_batch_destroy.restype = None
     lib.esp_set_timing.argtypes = [P, i32]
     lib.esp_set_timing.restype = ctypes.c_int
     lib.esp_last_timing.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -278,3 +305,96 @@ def debug_boys(precision, nmax: int, T: float) -> np.ndarray:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _check(load().esp_debug_boys(p, int(nmax), float(T), F.ctypes.data))
     return F
+
+
+class Batch:
+    """Many environments evaluated together (persistent kernel, CUDA graph).
+
+    The environments must outlive the batch, share one device and one
+    precision; positions and outputs are CUDA tensors (device memory)."""
+
+    def __init__(self, envs, stream=None):
+        lib = load()
+        self.envs = list(envs)
+        arr = (ctypes.c_void_p * len(self.envs))(*[e.handle.value for e in self.envs])
+        b = ctypes.c_void_p()
+        _check(lib.esp_batch_create(arr, len(self.envs), ctypes.c_void_p(int(stream) if stream is not None else 0),
+                                    ctypes.byref(b)))
+        self._b = b
+
+    def _arrays(self, positions, outs):
+        import torch
+        n = len(self.envs)
+        assert len(positions) == n
+        if outs is None:
+            outs = [torch.empty(int(p.shape[0]), dtype=torch.float64, device=p.device) for p in positions]
+        P = (ctypes.c_void_p * n)(*[p.data_ptr() if p.numel() else 0 for p in positions])
+        V = (ctypes.c_void_p * n)(*[v.data_ptr() if v.numel() else 0 for v in outs])
+        N = (ctypes.c_int64 * n)(*[int(p.shape[0]) for p in positions])
+        return P, N, V, outs
+
+    def eval(self, positions, outs=None):
+        P, N, V, outs = self._arrays(positions, outs)
+        _check(load().esp_batch_eval(self._b, P, N, V))
+        return outs
+
+    def set_shape(self, threads, ppt, split_scale=1.0):
+        _check(load().esp_batch_set_shape(self._b, int(threads), int(ppt), float(split_scale)))
+
+    def last_ms(self) -> float:
+        ms = ctypes.c_double()
+        _check(load().esp_batch_last_ms(self._b, ctypes.byref(ms)))
+        return ms.value
+
+    def signature(self, positions) -> str:
+        """Workload key for the autotune cache: environment sizes, position counts, device."""
+        import hashlib
+        import torch
+        parts = [torch.cuda.get_device_name(), str(len(self.envs))]
+        for e, p in zip(self.envs, positions):
+            i = e.info()
+            parts.append("%d:%d:%d:%d" % (i["n_distributions"], i["n_point_charges"], i["tile_size"], int(p.shape[0])))
+        return hashlib.sha256("|".join(parts).encode()).hexdigest()[:24]
+
+    def autotune(self, positions, outs=None, cache_path=None):
+        """Time the built launch shapes x split multipliers and keep the best.
+        With cache_path, a stored choice for the same workload key is reused."""
+        import json
+        import os
+        key = self.signature(positions)
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+            if key in cache:
+                c = cache[key]
+                self.set_shape(c["threads_per_block"], c["positions_per_thread"], c["split_scale"])
+                return dict(c, cached=True)
+        P, N, V, outs = self._arrays(positions, outs)
+        rep = TuneReport()
+        _check(load().esp_batch_autotune(self._b, P, N, V, ctypes.byref(rep)))
+        d = rep.as_dict()
+        if cache_path:
+            cache[key] = {k: d[k] for k in ("threads_per_block", "positions_per_thread", "split_scale", "best_ms")}
+            tmp = cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, cache_path)
+        return dict(d, cached=False)
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            load().esp_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

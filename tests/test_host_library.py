@@ -245,3 +245,14 @@ def test_onsite_monopoles_move_to_point_charges(lib):
     r1 = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, C[None])
     assert np.allclose(env.debug_host_eval(C[None]), r1, rtol=1e-12)
     assert np.allclose(env32.debug_host_eval(C[None]), r1, rtol=2e-7)
+
+
+def test_batch_refuses_host_only_contexts(lib):
+    import ctypes
+    wl = tiny_pd_environment(6, n_pairs=4, n_nuclei=1)
+    env = _host_env(wl)
+    arr = (ctypes.c_void_p * 1)(env.handle.value)
+    b = ctypes.c_void_p()
+    assert lib.esp_batch_create(arr, 1, None, ctypes.byref(b)) == esp.ESP_ERR_STATE
+    assert lib.esp_batch_create(arr, 0, None, ctypes.byref(b)) == esp.ESP_ERR_INVALID
+    lib.esp_batch_destroy(None)
