@@ -243,6 +243,86 @@ esp_status esp_batch_last_ms(esp_batch *b, double *ms);
 /* Free the batch (not its contexts).  NULL is a no-op. */
 void esp_batch_destroy(esp_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate of V over the QM region (the QM sphere about qm_center).
+ * V_sur = FP64 Legendre-product baseline + BF16 tensor-core MLP on the
+ * residual (64 Fourier features, 4 x 256 SiLU, scalar out), trained by the
+ * library's own forward/backward kernels and Adam on exact FP64 labels.  The
+ * exact kernel stays the fallback: positions in voxels whose validation error
+ * exceeded tol/2, near point charges, or picked by the online probe are
+ * evaluated exactly, and a failed probe withdraws its voxel for later calls.
+ * The paper has no surrogate; the exact sum it accelerates is the judge.
+ * ------------------------------------------------------------------------ */
+typedef struct esp_surrogate esp_surrogate;
+
+typedef struct {
+    int32_t size;              /* sizeof(esp_surrogate_cfg), set by esp_surrogate_default_cfg */
+    int32_t n_train;           /* training positions (2^22) */
+    int32_t n_valid;           /* validation positions for the trust map (2^18) */
+    int32_t epochs;            /* passes over the training set (6) */
+    int32_t batch;             /* mini-batch (8192) */
+    int32_t degree;            /* Legendre degree of the baseline (10; <= 16) */
+    double qm_radius;          /* radius of the QM sphere, bohr (6) */
+    double position_sd;        /* sd of the walker law for half the samples (2) */
+    double fourier_sigma;      /* sd of the Fourier frequencies, per unit radius (1) */
+    double lr;                 /* Adam learning rate, cosine-decayed (1e-3) */
+    double tol;                /* accepted error, Ha (2e-6): trust voxels at tol/2, probes at tol */
+    double voxel;              /* trust-map voxel edge, bohr (0.25) */
+    double nucleus_exclusion;  /* positions this close to a point charge fall back, bohr (0.5) */
+    int32_t probe_stride;      /* every probe_stride-th position is also evaluated exactly (64; 0 off) */
+    int32_t pad;
+    uint64_t seed;             /* positions, frequencies and initial weights (1011) */
+} esp_surrogate_cfg;
+
+typedef struct {
+    int64_t n_fallback;        /* positions of the last call evaluated exactly */
+    int64_t n_probe_fail;      /* probes that missed tol (last call; total in esp_surrogate_info) */
+    double surrogate_ms;       /* baseline + network time of the last call */
+    double total_ms;           /* the whole last call, fallback included */
+    double train_loss;         /* final training loss (normalised residual) */
+    double valid_max_err;      /* largest validation error of baseline + network, Ha */
+    double trusted_fraction;   /* share of visited voxels trusted */
+    int64_t n_params;          /* network parameters */
+    int64_t n_baseline;        /* baseline coefficients */
+    double valid_rms_err;      /* rms validation error of baseline + network, Ha */
+    double baseline_max_err;   /* the same two errors of the baseline alone (without the network) */
+    double baseline_rms_err;
+} esp_surrogate_stats;
+
+void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg);
+
+/* Train a surrogate of ctx's potential (ctx stays in use for labels and
+ * fallback; it must outlive the surrogate).  Synchronous.  Errors:
+ * ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_UNSUPPORTED, ESP_ERR_OOM, ESP_ERR_CUDA. */
+esp_status esp_surrogate_train(esp_ctx *ctx, const esp_surrogate_cfg *cfg, esp_surrogate **out);
+
+/* V_out[i] for device positions [n][3]: surrogate where trusted, exact
+ * elsewhere (see above).  Synchronous (one device->host read of the fallback
+ * count).  stats may be NULL. */
+esp_status esp_surrogate_eval(esp_surrogate *s, const double *positions, int64_t n, double *V_out,
+                              esp_surrogate_stats *stats);
+
+/* Baseline + network only (no fallback), device pointers; synchronous. */
+esp_status esp_surrogate_predict(esp_surrogate *s, const double *positions, int64_t n, double *V_out);
+
+esp_status esp_surrogate_info(const esp_surrogate *s, esp_surrogate_stats *stats);
+
+/* Versioned binary file with a checksum: configuration, baseline, frequencies,
+ * weights and trust map.  Loading binds the surrogate to ctx. */
+esp_status esp_surrogate_save(const esp_surrogate *s, const char *path);
+esp_status esp_surrogate_load(esp_ctx *ctx, const char *path, esp_surrogate **out);
+
+/* Test hooks: one forward + backward pass on a host batch (positions [n][3],
+ * normalised targets [n]) without updating; copies out the FP32 parameters,
+ * the gradient of mean((y - t)^2) (flat layout W1 b1 W2 b2 W3 b3 W4 b4 w5 b5)
+ * and the outputs y; and the Fourier frequencies [32][3] with
+ * (centre x, y, z, 1/R). */
+esp_status esp_surrogate_debug_step(esp_surrogate *s, const double *positions, const float *targets, int32_t n,
+                                    float *params_out, float *grad_out, float *y_out);
+esp_status esp_surrogate_features(const esp_surrogate *s, float *freq_out, double *centre_inv_r_out);
+
+void esp_surrogate_destroy(esp_surrogate *s);
+
 /* Switch the arithmetic of later evaluations (ESP_FP64 or ESP_FP32C). */
 esp_status esp_set_precision(esp_ctx *ctx, int32_t precision);
 

@@ -1,0 +1,478 @@
+// Kernels of the learned surrogate of V(r) over the QM region.
+//
+// Network: Fourier features gamma(u) = [sin(2 pi B u), cos(2 pi B u)] of the
+// position u = (r - centre) / R (32 frequencies, 64 features), four hidden
+// layers of 256 with SiLU, one linear output.  BF16 weights and activations,
+// FP32 accumulation on the tensor cores (mma.sync m16n8k16), FP32 master
+// weights updated by Adam.  The network models the residual of an FP64
+// polynomial baseline (products of Legendre polynomials in u), so that its
+// BF16 output only has to carry a small correction.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "surrogate_kernels.h"
+
+namespace esp {
+namespace sur {
+
+namespace {
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z)
+{
+    float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+
+// C[M x N] = op(A)[M x K] op(B)[K x N] (+ epilogue), 64 x 64 CTA tile, 4 warps
+// of 32 x 32, K in steps of 32.  op(A)[m][k] = A_T ? A[k lda + m] : A[m lda + k],
+// op(B)[k][n] = B_T ? B[n ldb + k] : B[k ldb + n].  grid.z splits K into
+// chunks of kchunk (partial results go to C + z * M * ldc).
+template <bool A_T, bool B_T>
+__global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD]; // stored [n][k]
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * g.kchunk;
+    const int kend = min(g.K, kbeg + g.kchunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gid = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                acc[i][j][r] = 0.0f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += 128) {
+            int mm = e / BK, kk = e % BK;
+            int m = m0 + mm, k = k0 + kk;
+            __nv_bfloat16 v = zero;
+            if (m < g.M && k < kend)
+                v = A_T ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
+            As[mm][kk] = v;
+        }
+        for (int e = threadIdx.x; e < BN * BK; e += 128) {
+            int nn = e / BK, kk = e % BK;
+            int n = n0 + nn, k = k0 + kk;
+            __nv_bfloat16 v = zero;
+            if (n < g.N && k < kend)
+                v = B_T ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
+            Bs[nn][kk] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + gid;
+                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 2 * tig]);
+                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 2 * tig]);
+                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 8 + 2 * tig]);
+                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 8 + 2 * tig]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + gid;
+                bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][ks + 2 * tig]);
+                bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][ks + 8 + 2 * tig]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_bf16_16816(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + j * 8 + 2 * tig + (r & 1);
+                if (m >= g.M || n >= g.N)
+                    continue;
+                float v = acc[i][j][r];
+                const size_t o = (size_t)m * g.ldc + n;
+                switch (g.epi) {
+                case kEpiSiluFwd: { // Z = acc + b; keep Z, emit SiLU(Z)
+                    float z = v + g.bias[n];
+                    if (g.Cf)
+                        g.Cf[o] = z;
+                    g.Cb[o] = __float2bfloat16(silu(z));
+                    break;
+                }
+                case kEpiGradSilu: // dZ_prev = acc * SiLU'(Z_prev)
+                    g.Cb[o] = __float2bfloat16(v * silu_grad(g.aux[o]));
+                    break;
+                default: // raw FP32 (split-K partials)
+                    g.Cf[(size_t)blockIdx.z * g.M * g.ldc + o] = v;
+                }
+            }
+        }
+    }
+}
+
+__global__ void features_kernel(const double *__restrict__ pos, int n, const float *__restrict__ freq, double cx,
+                                double cy, double cz, double inv_r, __nv_bfloat16 *__restrict__ X)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float ux = float((pos[3 * i] - cx) * inv_r), uy = float((pos[3 * i + 1] - cy) * inv_r),
+                uz = float((pos[3 * i + 2] - cz) * inv_r);
+#pragma unroll 4
+    for (int f = 0; f < kFreq; ++f) {
+        float ph = 6.283185307179586f * (freq[3 * f] * ux + freq[3 * f + 1] * uy + freq[3 * f + 2] * uz);
+        float s, c;
+        __sincosf(ph, &s, &c);
+        X[(size_t)i * kFeat + f] = __float2bfloat16(s);
+        X[(size_t)i * kFeat + kFreq + f] = __float2bfloat16(c);
+    }
+}
+
+// y[i] = sum_k H[i][k] w[k] + b; with targets: dy = 2 (y - t) / n, loss partial.
+__global__ void output_kernel(const __nv_bfloat16 *__restrict__ H, int n, const float *__restrict__ w,
+                              const float *__restrict__ bptr,
+                              float *__restrict__ y, const float *__restrict__ t, float *__restrict__ dy,
+                              float *__restrict__ loss_part)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    float l = 0.0f;
+    if (warp < n) {
+        float s = 0.0f;
+        for (int k = lane; k < kHidden; k += 32)
+            s += __bfloat162float(H[(size_t)warp * kHidden + k]) * w[k];
+        for (int o = 16; o; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        s += *bptr;
+        if (lane == 0) {
+            y[warp] = s;
+            if (t) {
+                float r = s - t[warp];
+                dy[warp] = 2.0f * r / float(n);
+                l = r * r;
+            }
+        }
+    }
+    if (loss_part && lane == 0 && warp < n)
+        loss_part[warp] = l;
+}
+
+// dZ4[i][k] = dy[i] w[k] SiLU'(Z4[i][k]) (bf16); gradient of the output layer
+// parameters is accumulated by out_grad_kernel.
+__global__ void out_back_kernel(const float *__restrict__ dy, int n, const float *__restrict__ w,
+                                const float *__restrict__ Z, __nv_bfloat16 *__restrict__ dZ)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)n * kHidden)
+        return;
+    const int i = int(e / kHidden), k = int(e % kHidden);
+    dZ[e] = __float2bfloat16(dy[i] * w[k] * silu_grad(Z[e]));
+}
+
+// per-block partials of dw[k] = sum_i dy[i] H[i][k] and db = sum_i dy[i]
+__global__ void out_grad_kernel(const float *__restrict__ dy, const __nv_bfloat16 *__restrict__ H, int n, int rows,
+                                float *__restrict__ part)
+{
+    const int k = threadIdx.x; // blockDim = 256 = kHidden
+    const int r0 = blockIdx.x * rows, r1 = min(n, r0 + rows);
+    float s = 0.0f, sb = 0.0f;
+    for (int i = r0; i < r1; ++i) {
+        s += dy[i] * __bfloat162float(H[(size_t)i * kHidden + k]);
+        sb += dy[i];
+    }
+    part[(size_t)blockIdx.x * (kHidden + 1) + k] = s;
+    if (k == 0)
+        part[(size_t)blockIdx.x * (kHidden + 1) + kHidden] = sb;
+}
+
+// per-block partial column sums of a BF16 [n x 256] matrix
+__global__ void colsum_kernel(const __nv_bfloat16 *__restrict__ M, int n, int rows, float *__restrict__ part)
+{
+    const int k = threadIdx.x;
+    const int r0 = blockIdx.x * rows, r1 = min(n, r0 + rows);
+    float s = 0.0f;
+    for (int i = r0; i < r1; ++i)
+        s += __bfloat162float(M[(size_t)i * kHidden + k]);
+    part[(size_t)blockIdx.x * kHidden + k] = s;
+}
+
+// out[j] = sum_z part[z][j] in a fixed order
+__global__ void sum_parts_kernel(const float *__restrict__ part, int nparts, int len, float *__restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len)
+        return;
+    float s = 0.0f;
+    for (int z = 0; z < nparts; ++z)
+        s += part[(size_t)z * len + j];
+    out[j] = s;
+}
+
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, int n, float lr, float b1,
+                            float b2, float c1, float c2, float eps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.0f - b1) * gi;
+    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    w[i] = wi;
+    if (wb)
+        wb[i] = __float2bfloat16(wi);
+}
+
+// V[i] = baseline(u) + scale * y[i] (FP64 baseline: sum_c coef[c] P_a(ux) P_b(uy) P_c(uz))
+__global__ void combine_kernel(const double *__restrict__ pos, int n, double cx, double cy, double cz,
+                               double inv_r, const double *__restrict__ coef, const int *__restrict__ powers,
+                               int ncoef, int degree, const float *__restrict__ y, double scale,
+                               double *__restrict__ V)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    double u[3] = {(pos[3 * i] - cx) * inv_r, (pos[3 * i + 1] - cy) * inv_r, (pos[3 * i + 2] - cz) * inv_r};
+    double P[3][kMaxDegree + 1];
+    for (int d = 0; d < 3; ++d) {
+        P[d][0] = 1.0;
+        if (degree >= 1)
+            P[d][1] = u[d];
+        for (int l = 1; l < degree; ++l)
+            P[d][l + 1] = ((2 * l + 1) * u[d] * P[d][l] - l * P[d][l - 1]) / (l + 1);
+    }
+    double s = 0.0;
+    for (int c = 0; c < ncoef; ++c)
+        s += coef[c] * P[0][powers[3 * c]] * P[1][powers[3 * c + 1]] * P[2][powers[3 * c + 2]];
+    V[i] = s + scale * (double)y[i];
+}
+
+// Fallback flags: untrusted voxel, outside the map, or probe position.
+__global__ void flag_kernel(const double *__restrict__ pos, int n, double cx, double cy, double cz, double vox,
+                            int dim, const unsigned char *__restrict__ trust, int probe_stride, int probe_offset,
+                            int *__restrict__ flag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const double h = 0.5 * dim * vox;
+    int ix = int(floor((pos[3 * i] - cx + h) / vox)), iy = int(floor((pos[3 * i + 1] - cy + h) / vox)),
+        iz = int(floor((pos[3 * i + 2] - cz + h) / vox));
+    bool inside = ix >= 0 && iy >= 0 && iz >= 0 && ix < dim && iy < dim && iz < dim;
+    bool ok = inside && trust[((size_t)ix * dim + iy) * dim + iz];
+    bool probe = probe_stride > 0 && (i % probe_stride) == probe_offset;
+    flag[i] = (!ok || probe) ? 1 : 0;
+}
+
+// Exclusive scan of flags within blocks of 1024; block totals to `tot`.
+__global__ void scan_block_kernel(const int *__restrict__ flag, int n, int *__restrict__ pre, int *__restrict__ tot)
+{
+    __shared__ int s[1024];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    int v = i < n ? flag[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n)
+        pre[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == 1023)
+        tot[blockIdx.x] = s[1023];
+}
+
+// Exclusive scan of block totals (one thread; the number of blocks is small).
+__global__ void scan_tot_kernel(int *__restrict__ tot, int nb, int *__restrict__ count)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    int run = 0;
+    for (int b = 0; b < nb; ++b) {
+        int t = tot[b];
+        tot[b] = run;
+        run += t;
+    }
+    *count = run;
+}
+
+__global__ void compact_kernel(const double *__restrict__ pos, const int *__restrict__ flag,
+                               const int *__restrict__ pre, const int *__restrict__ tot, int n,
+                               double *__restrict__ cpos, int *__restrict__ cidx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i])
+        return;
+    const int j = pre[i] + tot[i / 1024];
+    cpos[3 * j] = pos[3 * i];
+    cpos[3 * j + 1] = pos[3 * i + 1];
+    cpos[3 * j + 2] = pos[3 * i + 2];
+    cidx[j] = i;
+}
+
+// Scatter exact values back; probe positions whose surrogate value missed by
+// more than tol mark their voxel untrusted for later calls.
+__global__ void scatter_kernel(const double *__restrict__ cV, const int *__restrict__ cidx, const int *__restrict__ count,
+                               double *__restrict__ V, const double *__restrict__ pos, double cx, double cy,
+                               double cz, double vox, int dim, unsigned char *__restrict__ trust, int probe_stride,
+                               int probe_offset, double tol, int *__restrict__ n_fail)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *count)
+        return;
+    const int i = cidx[j];
+    const double exact = cV[j];
+    if (probe_stride > 0 && (i % probe_stride) == probe_offset && fabs(V[i] - exact) > tol) {
+        const double h = 0.5 * dim * vox;
+        int ix = int(floor((pos[3 * i] - cx + h) / vox)), iy = int(floor((pos[3 * i + 1] - cy + h) / vox)),
+            iz = int(floor((pos[3 * i + 2] - cz + h) / vox));
+        if (ix >= 0 && iy >= 0 && iz >= 0 && ix < dim && iy < dim && iz < dim)
+            trust[((size_t)ix * dim + iy) * dim + iz] = 0;
+        atomicAdd(n_fail, 1);
+    }
+    V[i] = exact;
+}
+
+} // namespace
+
+cudaError_t gemm(bool a_t, bool b_t, const GemmArgs &g, int ksplit, cudaStream_t s)
+{
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ksplit);
+    if (!a_t && !b_t)
+        gemm_kernel<false, false><<<grid, 128, 0, s>>>(g);
+    else if (!a_t && b_t)
+        gemm_kernel<false, true><<<grid, 128, 0, s>>>(g);
+    else if (a_t && !b_t)
+        gemm_kernel<true, false><<<grid, 128, 0, s>>>(g);
+    else
+        gemm_kernel<true, true><<<grid, 128, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t features(const double *pos, int n, const float *freq, const double c[3], double inv_r,
+                     __nv_bfloat16 *X, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    features_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos, n, freq, c[0], c[1], c[2], inv_r, X);
+    return cudaGetLastError();
+}
+
+cudaError_t output(const __nv_bfloat16 *H, int n, const float *w, const float *b, float *y, const float *t, float *dy,
+                   float *loss_part, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    output_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(H, n, w, b, y, t, dy, loss_part);
+    return cudaGetLastError();
+}
+
+cudaError_t out_back(const float *dy, int n, const float *w, const float *Z, __nv_bfloat16 *dZ, cudaStream_t s)
+{
+    size_t tot = (size_t)n * kHidden;
+    out_back_kernel<<<unsigned((tot + 255) / 256), 256, 0, s>>>(dy, n, w, Z, dZ);
+    return cudaGetLastError();
+}
+
+cudaError_t out_grad(const float *dy, const __nv_bfloat16 *H, int n, float *part, int nparts, float *out,
+                     cudaStream_t s)
+{
+    const int rows = (n + nparts - 1) / nparts;
+    out_grad_kernel<<<nparts, kHidden, 0, s>>>(dy, H, n, rows, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    return sum_parts(part, nparts, kHidden + 1, out, s);
+}
+
+cudaError_t colsum(const __nv_bfloat16 *M, int n, float *part, int nparts, float *out, cudaStream_t s)
+{
+    const int rows = (n + nparts - 1) / nparts;
+    colsum_kernel<<<nparts, kHidden, 0, s>>>(M, n, rows, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    return sum_parts(part, nparts, kHidden, out, s);
+}
+
+cudaError_t sum_parts(const float *part, int nparts, int len, float *out, cudaStream_t s)
+{
+    sum_parts_kernel<<<(len + 255) / 256, 256, 0, s>>>(part, nparts, len, out);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(float *w, const float *g, float *m, float *v, __nv_bfloat16 *wb, int n, float lr, float b1,
+                 float b2, int step, float eps, cudaStream_t s)
+{
+    const float c1 = 1.0f / (1.0f - powf(b1, float(step))), c2 = 1.0f / (1.0f - powf(b2, float(step)));
+    adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, wb, n, lr, b1, b2, c1, c2, eps);
+    return cudaGetLastError();
+}
+
+cudaError_t combine(const double *pos, int n, const double c[3], double inv_r, const double *coef, const int *powers,
+                    int ncoef, int degree, const float *y, double scale, double *V, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    combine_kernel<<<(n + 127) / 128, 128, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, powers, ncoef, degree, y,
+                                                   scale, V);
+    return cudaGetLastError();
+}
+
+cudaError_t fallback_select(const double *pos, int n, const double c[3], double vox, int dim,
+                            const unsigned char *trust, int probe_stride, int probe_offset, int *flag, int *pre,
+                            int *tot, int *count, double *cpos, int *cidx, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    flag_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos, n, c[0], c[1], c[2], vox, dim, trust, probe_stride,
+                                                probe_offset, flag);
+    const int nb = (n + 1023) / 1024;
+    scan_block_kernel<<<nb, 1024, 0, s>>>(flag, n, pre, tot);
+    scan_tot_kernel<<<1, 1, 0, s>>>(tot, nb, count);
+    compact_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos, flag, pre, tot, n, cpos, cidx);
+    return cudaGetLastError();
+}
+
+cudaError_t fallback_scatter(const double *cV, const int *cidx, const int *count, int n_max, double *V,
+                             const double *pos, const double c[3], double vox, int dim, unsigned char *trust,
+                             int probe_stride, int probe_offset, double tol, int *n_fail, cudaStream_t s)
+{
+    if (n_max <= 0)
+        return cudaSuccess;
+    scatter_kernel<<<(n_max + 255) / 256, 256, 0, s>>>(cV, cidx, count, V, pos, c[0], c[1], c[2], vox, dim, trust,
+                                                       probe_stride, probe_offset, tol, n_fail);
+    return cudaGetLastError();
+}
+
+} // namespace sur
+} // namespace esp

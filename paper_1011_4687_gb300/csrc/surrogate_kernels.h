@@ -1,0 +1,58 @@
+// Launch interface of the surrogate kernels (see surrogate_kernels.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace esp {
+namespace sur {
+
+constexpr int kFreq = 32;       // Fourier frequencies
+constexpr int kFeat = 64;       // features: sin and cos of each frequency
+constexpr int kHidden = 256;    // width of each hidden layer
+constexpr int kLayers = 4;      // hidden layers
+constexpr int kMaxDegree = 16;  // largest Legendre degree of the baseline
+
+enum { kEpiSiluFwd = 0, kEpiGradSilu = 1, kEpiRaw = 2 };
+
+struct GemmArgs {
+    int M, N, K;
+    const __nv_bfloat16 *A;
+    int lda;
+    const __nv_bfloat16 *B;
+    int ldb;
+    float *Cf;            // FP32 output (Z for kEpiSiluFwd, partials for kEpiRaw)
+    __nv_bfloat16 *Cb;    // BF16 output
+    int ldc;
+    const float *bias;    // [N] (kEpiSiluFwd)
+    const float *aux;     // [M][ldc] pre-activation of the previous layer (kEpiGradSilu)
+    int epi;
+    int kchunk;           // K range of one grid.z slice
+};
+
+cudaError_t gemm(bool a_t, bool b_t, const GemmArgs &g, int ksplit, cudaStream_t s);
+cudaError_t features(const double *pos, int n, const float *freq, const double c[3], double inv_r,
+                     __nv_bfloat16 *X, cudaStream_t s);
+// y[i] = H[i] . w + *b; with targets t: dy = 2 (y - t) / n and squared errors
+cudaError_t output(const __nv_bfloat16 *H, int n, const float *w, const float *b, float *y, const float *t, float *dy,
+                   float *loss_part, cudaStream_t s);
+cudaError_t out_back(const float *dy, int n, const float *w, const float *Z, __nv_bfloat16 *dZ, cudaStream_t s);
+cudaError_t out_grad(const float *dy, const __nv_bfloat16 *H, int n, float *part, int nparts, float *out,
+                     cudaStream_t s);
+// out[k] = sum_i M[i][k] for a BF16 [n x 256] matrix (fixed-order partials)
+cudaError_t colsum(const __nv_bfloat16 *M, int n, float *part, int nparts, float *out, cudaStream_t s);
+cudaError_t sum_parts(const float *part, int nparts, int len, float *out, cudaStream_t s);
+cudaError_t adam(float *w, const float *g, float *m, float *v, __nv_bfloat16 *wb, int n, float lr, float b1,
+                 float b2, int step, float eps, cudaStream_t s);
+cudaError_t combine(const double *pos, int n, const double c[3], double inv_r, const double *coef, const int *powers,
+                    int ncoef, int degree, const float *y, double scale, double *V, cudaStream_t s);
+cudaError_t fallback_select(const double *pos, int n, const double c[3], double vox, int dim,
+                            const unsigned char *trust, int probe_stride, int probe_offset, int *flag, int *pre,
+                            int *tot, int *count, double *cpos, int *cidx, cudaStream_t s);
+cudaError_t fallback_scatter(const double *cV, const int *cidx, const int *count, int n_max, double *V,
+                             const double *pos, const double c[3], double vox, int dim, unsigned char *trust,
+                             int probe_stride, int probe_offset, double tol, int *n_fail, cudaStream_t s);
+
+} // namespace sur
+} // namespace esp

@@ -70,6 +70,26 @@ class TuneReport(ctypes.Structure):
                            "split_scale": self.tried_scale[i], "ms": self.tried_ms[i]} for i in range(n)]}
 
 
+class SurrogateCfg(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_int32), ("n_train", ctypes.c_int32), ("n_valid", ctypes.c_int32),
+                ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("degree", ctypes.c_int32),
+                ("qm_radius", ctypes.c_double), ("position_sd", ctypes.c_double), ("fourier_sigma", ctypes.c_double),
+                ("lr", ctypes.c_double), ("tol", ctypes.c_double), ("voxel", ctypes.c_double),
+                ("nucleus_exclusion", ctypes.c_double), ("probe_stride", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class SurrogateStats(ctypes.Structure):
+    _fields_ = [("n_fallback", ctypes.c_int64), ("n_probe_fail", ctypes.c_int64), ("surrogate_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("train_loss", ctypes.c_double), ("valid_max_err", ctypes.c_double),
+                ("trusted_fraction", ctypes.c_double), ("n_params", ctypes.c_int64), ("n_baseline", ctypes.c_int64),
+                ("valid_rms_err", ctypes.c_double), ("baseline_max_err", ctypes.c_double),
+                ("baseline_rms_err", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 EXPORTED = ["esp_default_options", "esp_create", "esp_eval", "esp_eval_walkers", "esp_set_precision",
             "esp_get_info", "esp_synchronize", "esp_destroy", "esp_status_string", "esp_last_error",
             "esp_abi_version", "esp_debug_boys", "esp_debug_host_eval", "esp_set_timing", "esp_last_timing"]
@@ -132,6 +152,26 @@ def load(build_if_missing: bool = False):
     lib.esp_batch_last_ms.restype = ctypes.c_int
     lib.esp_batch_destroy.argtypes = [P]
     lib.esp_batch_destroy.restype = None
+    lib.esp_surrogate_default_cfg.argtypes = [ctypes.POINTER(SurrogateCfg)]
+    lib.esp_surrogate_default_cfg.restype = None
+    lib.esp_surrogate_train.argtypes = [P, ctypes.POINTER(SurrogateCfg), ctypes.POINTER(P)]
+    lib.esp_surrogate_train.restype = ctypes.c_int
+    lib.esp_surrogate_eval.argtypes = [P, P, i64, P, ctypes.POINTER(SurrogateStats)]
+    lib.esp_surrogate_eval.restype = ctypes.c_int
+    lib.esp_surrogate_predict.argtypes = [P, P, i64, P]
+    lib.esp_surrogate_predict.restype = ctypes.c_int
+    lib.esp_surrogate_info.argtypes = [P, ctypes.POINTER(SurrogateStats)]
+    lib.esp_surrogate_info.restype = ctypes.c_int
+    lib.esp_surrogate_save.argtypes = [P, ctypes.c_char_p]
+    lib.esp_surrogate_save.restype = ctypes.c_int
+    lib.esp_surrogate_load.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(P)]
+    lib.esp_surrogate_load.restype = ctypes.c_int
+    lib.esp_surrogate_debug_step.argtypes = [P, P, P, i32, P, P, P]
+    lib.esp_surrogate_debug_step.restype = ctypes.c_int
+    lib.esp_surrogate_features.argtypes = [P, P, P]
+    lib.esp_surrogate_features.restype = ctypes.c_int
+    lib.esp_surrogate_destroy.argtypes = [P]
+    lib.esp_surrogate_destroy.restype = None
     lib.esp_set_timing.argtypes = [P, i32]
     lib.esp_set_timing.restype = ctypes.c_int
     lib.esp_last_timing.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -386,6 +426,96 @@ class Batch:
         if getattr(self, "_b", None) and self._b.value:
             load().esp_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+N_SURROGATE_PARAMS = 64 * 256 + 256 + 3 * (256 * 256 + 256) + 256 + 1
+
+
+class Surrogate:
+    """Learned surrogate of an Environment's potential over its QM sphere,
+    with exact fallback (see include/esp.h)."""
+
+    def __init__(self, env, _handle=None, **cfg):
+        self.env = env
+        if _handle is not None:
+            self._s = _handle
+            return
+        lib = load()
+        c = SurrogateCfg()
+        lib.esp_surrogate_default_cfg(ctypes.byref(c))
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        h = ctypes.c_void_p()
+        _check(lib.esp_surrogate_train(env.handle, ctypes.byref(c), ctypes.byref(h)))
+        self._s = h
+
+    @staticmethod
+    def load(env, path):
+        h = ctypes.c_void_p()
+        _check(load().esp_surrogate_load(env.handle, path.encode(), ctypes.byref(h)))
+        return Surrogate(env, _handle=h)
+
+    def save(self, path):
+        _check(load().esp_surrogate_save(self._s, path.encode()))
+
+    def eval(self, positions, out=None):
+        """(V, stats) for a CUDA tensor of positions [n, 3]."""
+        import torch
+        n = int(positions.shape[0])
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=positions.device)
+        st = SurrogateStats()
+        _check(load().esp_surrogate_eval(self._s, ctypes.c_void_p(positions.data_ptr()), n,
+                                          ctypes.c_void_p(out.data_ptr()), ctypes.byref(st)))
+        return out, st.as_dict()
+
+    def predict(self, positions, out=None):
+        import torch
+        n = int(positions.shape[0])
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=positions.device)
+        _check(load().esp_surrogate_predict(self._s, ctypes.c_void_p(positions.data_ptr()), n,
+                                             ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def info(self) -> dict:
+        st = SurrogateStats()
+        _check(load().esp_surrogate_info(self._s, ctypes.byref(st)))
+        return st.as_dict()
+
+    def debug_step(self, positions: np.ndarray, targets: np.ndarray):
+        """(params, grad, y) of one forward/backward pass on a host batch (no update)."""
+        pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+        t = np.ascontiguousarray(targets, np.float32)
+        params = np.zeros(N_SURROGATE_PARAMS, np.float32)
+        grad = np.zeros(N_SURROGATE_PARAMS, np.float32)
+        y = np.zeros(pos.shape[0], np.float32)
+        _check(load().esp_surrogate_debug_step(self._s, pos.ctypes.data, t.ctypes.data, pos.shape[0],
+                                                params.ctypes.data, grad.ctypes.data, y.ctypes.data))
+        return params, grad, y
+
+    def features(self):
+        freq = np.zeros((32, 3), np.float32)
+        ci = np.zeros(4)
+        _check(load().esp_surrogate_features(self._s, freq.ctypes.data, ci.ctypes.data))
+        return freq, ci[:3].copy(), float(ci[3])
+
+    def close(self):
+        if getattr(self, "_s", None) and self._s.value:
+            load().esp_surrogate_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:
