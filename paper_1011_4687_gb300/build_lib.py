@@ -4,7 +4,9 @@
 
 Produces paper_1011_4687_gb300/_lib/libesp_gb300.so from csrc/ with nvcc
 (one -gencode: compute_103a / sm_103a) and g++ for the host-only builder.
-Translation units compile in parallel; nothing else is built.
+csrc/esp_shape.cu is compiled once per launch shape listed in
+csrc/esp_shapes.h (one object each); all translation units compile in
+parallel; nothing else is built.
 """
 from __future__ import annotations
 
@@ -12,6 +14,7 @@ import argparse
 import concurrent.futures as cf
 import glob
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -35,13 +38,36 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the library")
 
 
+SHAPE_SRC = os.path.join(CSRC, "esp_shape.cu")
+SHAPE_LISTS = os.path.join(CSRC, "esp_shapes.h")
+
+
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    return sorted(p for p in glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp"))
+                  if p != SHAPE_SRC)
+
+
+def shape_jobs():
+    """(object name, -D flags) for every launch shape listed in esp_shapes.h."""
+    with open(SHAPE_LISTS) as f:
+        text = f.read()
+    jobs = []
+    for fam in ("F32C", "F64", "BATCH"):
+        m = re.search(r"#define ESP_%s_SHAPES\(X\)(.*)" % fam, text)
+        if not m:
+            raise RuntimeError("esp_shapes.h: no ESP_%s_SHAPES list" % fam)
+        for args in re.findall(r"X\(([^)]*)\)", m.group(1)):
+            v = [int(x) for x in args.split(",")]
+            flags = ["-DESP_SHAPE_%s" % fam, "-DESP_NT=%d" % v[0], "-DESP_PPT=%d" % v[1]]
+            if fam == "BATCH":
+                flags.append("-DESP_PREC=%d" % v[2])
+            jobs.append(("esp_shape_%s_%s.o" % (fam.lower(), "_".join(map(str, v))), flags))
+    return jobs
 
 
 def _inputs():
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "esp.h"),
-                                                               os.path.abspath(__file__)]
+    return (sources() + [SHAPE_SRC] + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+            + [os.path.join(ROOT, "include", "esp.h"), os.path.abspath(__file__)])
 
 
 def is_stale() -> bool:
@@ -51,9 +77,10 @@ def is_stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _inputs())
 
 
-def _compile(src: str, obj: str, verbose: bool, ptxas_v: bool) -> str:
+def _compile(src: str, obj: str, verbose: bool, ptxas_v: bool, defines=()) -> str:
     if src.endswith(".cu"):
-        cmd = [_nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_v else []) + ["-c", src, "-o", obj]
+        cmd = ([_nvcc()] + NVCC_FLAGS + list(defines) + (["-Xptxas", "-v"] if ptxas_v else [])
+               + ["-c", src, "-o", obj])
     else:
         cmd = [os.environ.get("CXX", "g++")] + CXX_FLAGS + ["-c", src, "-o", obj]
     if verbose:
@@ -68,16 +95,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     if not force and not is_stale():
         return LIB
     os.makedirs(os.path.join(OUT, "obj"), exist_ok=True)
-    srcs = sources()
-    objs = [os.path.join(OUT, "obj", os.path.basename(s) + ".o") for s in srcs]
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        logs = list(ex.map(lambda so: _compile(so[0], so[1], verbose, ptxas_v), zip(srcs, objs)))
+    jobs = [(s, os.path.join(OUT, "obj", os.path.basename(s) + ".o"), ()) for s in sources()]
+    jobs += [(SHAPE_SRC, os.path.join(OUT, "obj", name), flags) for name, flags in shape_jobs()]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        logs = list(ex.map(lambda j: _compile(j[0], j[1], verbose, ptxas_v, j[2]), jobs))
+    objs = [j[1] for j in jobs]
     if ptxas_v:
-        for s, log in zip(srcs, logs):
+        for j, log in zip(jobs, logs):
             if log.strip():
-                print("== %s\n%s" % (os.path.basename(s), log))
+                print("== %s\n%s" % (os.path.basename(j[1]), log))
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+    cmd = ([_nvcc()] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs
+           + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"])
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
