@@ -124,7 +124,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("esp_kernels.cu", "esp_internal.h", "esp_eval_core.h"):
+    for name in ("esp_potential.cuh", "esp_shape.cu", "esp_internal.h", "esp_eval_core.h"):
         with open(os.path.join(ROOT, "paper_1011_4687_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -163,6 +163,150 @@ def sample_indices(wl):
     outer = np.argsort(-r)[:32]
     ws = [0, wl.n_walkers - 1]
     return ws, np.concatenate([np.arange(w * wl.n_elec, (w + 1) * wl.n_elec) for w in ws] + [outer])
+
+
+def _gen_batched(n_sys):
+    """The batched workload's systems, generated in a spawn-started process
+    pool (numpy only; no CUDA in the workers)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from workloads import batched_specs, batched_system
+    specs = batched_specs(n_sys=n_sys)
+    order = sorted(range(len(specs)), key=lambda k: -specs[k]["n_atoms"])
+    out = [None] * len(specs)
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        futs = {ex.submit(batched_system, specs[k]): k for k in order}
+        for f in cf.as_completed(futs):
+            out[futs[f]] = f.result()
+    return out
+
+
+def batch_leg(args, esp, torch, stream, flush, wls):
+    """Many uneven systems in one persistent, graph-replayed batch (tuned
+    launch shape) against the same systems evaluated one esp_eval at a time."""
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:  # the pair builder runs outside the GIL
+        envs = list(ex.map(lambda w: esp.Environment(w.nuclei_xyz, w.nuclei_Z, w.pairs, precision="fp32c",
+                                                     stream=stream.cuda_stream), wls))
+    pos = [torch.from_numpy(w.positions.reshape(-1, 3)).cuda() for w in wls]
+    outs = [torch.empty(int(p.shape[0]), dtype=torch.float64, device="cuda") for p in pos]
+    units = [e.info()["n_distributions"] + e.info()["n_point_charges"] for e in envs]
+    evals = sum(u * int(p.shape[0]) for u, p in zip(units, pos))
+    b = esp.Batch(envs, stream=stream.cuda_stream)
+    tune = b.autotune(pos, outs)
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            flush.zero_()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            s1.record(stream)
+            s1.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        return statistics.mean(ts)
+
+    def singles():
+        for e, p, o in zip(envs, pos, outs):
+            e.eval(p, out=o) if p.shape[0] else None
+
+    for _ in range(max(1, args.warmup)):
+        b.eval(pos, outs)
+        singles()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 3))
+    ms_b = timed(lambda: b.eval(pos, outs), k)
+    ms_s = timed(singles, k)
+    res = {"workload": "%d systems, %d-%d distributions, %d-%d positions (log-uniform sizes)"
+                       % (len(wls), min(units), max(units), min(int(p.shape[0]) for p in pos),
+                          max(int(p.shape[0]) for p in pos)),
+           "value": evals / (ms_b * 1e-3), "unit": "evals/s", "ms_per_step": ms_b,
+           "evals_per_step": evals, "separate_evals_ms": ms_s, "speedup_vs_separate": ms_s / ms_b,
+           "tuned_shape": {k2: tune[k2] for k2 in ("threads_per_block", "positions_per_thread", "split_scale")},
+           "gpu_launches_per_step": 3}
+    b.close()
+    for e in envs:
+        e.close()
+    return res
+
+
+def surrogate_leg(args, esp, torch, stream, flush, oracle_mod):
+    """The learned surrogate with exact fallback on the small environment
+    (200 nuclei + 2,000 s-charges), trained with the library defaults (2^22
+    positions labelled by the exact kernel), evaluated at 131,072 positions per
+    step, against the exact FP32C sum of the same positions."""
+    from workloads import qm_positions, seed_for_config, small_environment
+    wl = small_environment(seed=seed_for_config(1))
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
+    units = env.info()["n_distributions"] + env.info()["n_point_charges"]
+    t0 = time.perf_counter()
+    sur = esp.Surrogate(env)
+    t_train = time.perf_counter() - t0
+    n = 131072
+    pos_np = qm_positions(np.random.default_rng(seed_for_config(4)), n)
+    pos = torch.from_numpy(pos_np).cuda()
+    Vs = torch.empty(n, dtype=torch.float64, device="cuda")
+    Vx = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        sur.eval(pos, Vs)
+        env.eval(pos, out=Vx)
+    torch.cuda.synchronize()
+    ts, tx, fb = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, st = sur.eval(pos, Vs)
+        ts.append(time.perf_counter() - t1)
+        fb.append(st["n_fallback"])
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        env.eval(pos, out=Vx)
+        torch.cuda.synchronize()
+        tx.append(time.perf_counter() - t1)
+    ms_s, ms_x = statistics.mean(ts) * 1e3, statistics.mean(tx) * 1e3
+    # the network + baseline alone (no fallback): one fused tensor-core launch
+    Vp = torch.empty(n, dtype=torch.float64, device="cuda")
+    sur.predict(pos, Vp)
+    tp = []
+    for _ in range(args.steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        sur.predict(pos, Vp)
+        s1.record(stream)
+        s1.synchronize()
+        tp.append(s0.elapsed_time(s1))
+    ms_p = statistics.mean(tp)
+    info = sur.info()
+    res = {"workload": "small environment (%d point charges + %d s-charges), %d positions per step"
+                       % (wl.nuclei_Z.size, env.info()["n_distributions"], n),
+           "value": units * n / (ms_s * 1e-3), "unit": "equivalent evals/s", "ms_per_step": ms_s,
+           "exact_fp32c_ms": ms_x, "speedup_vs_exact_fp32c": ms_x / ms_s,
+           "fallback_fraction": statistics.mean(fb) / n, "train_s": t_train,
+           "valid_rms_err_ha": info["valid_rms_err"], "baseline_only_rms_err_ha": info["baseline_rms_err"],
+           "trusted_voxel_fraction": info["trusted_fraction"],
+           "predict_only_ms": ms_p, "predict_only_positions_per_s": n / (ms_p * 1e-3),
+           "predict_only_tflops": n * 2.0 * (64 * 256 + 3 * 256 * 256 + 256) / (ms_p * 1e-3) / 1e12,
+           "inference": "one fused tcgen05 kernel per call (BF16 x BF16 -> FP32 in TMEM); training GEMMs mma.sync"}
+    if oracle_mod is not None:
+        m = 64 * 32  # 64 whole walkers of 32 electrons
+        ref = oracle_mod.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos_np[:m])
+        got = Vs[:m].cpu().numpy()
+        res["predict_only_rms_err_ha"] = float(np.sqrt(np.mean((Vp[:m].cpu().numpy() - ref) ** 2)))
+        Eg = -got.reshape(64, 32).sum(1)
+        Er = oracle_mod.walker_energies(ref, 64, 32)
+        res["accuracy"] = {"sample": "64 walkers x 32 electrons vs the FP64 oracle",
+                           "max_point_err_ha": float(np.abs(got - ref).max()),
+                           "max_walker_err_ha": float(np.abs(Eg - Er).max())}
+    sur.close()
+    env.close()
+    return res
 
 
 def run_reference(args):
@@ -206,12 +350,20 @@ def main(argv=None):
     ap.add_argument("--fp64-walkers", type=int, default=256, help="walkers in the FP64 rate measurement")
     ap.add_argument("--ref-positions", type=int, default=32, help="positions per oracle step (reference arm)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-systems leg")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched leg")
     ap.add_argument("--walkers", type=int, default=4096,
                     help="walkers of 32 electrons per GPU (the benchmark workload is 4096; fewer only for profiling)")
     args = ap.parse_args(argv)
     keep_heap()
     if args.impl == "reference":
         return run_reference(args)
+
+    # the batched leg's systems come from a spawn-started pool, before any CUDA call
+    batch_wls = None
+    if not args.no_batch and int(os.environ.get("RANK", "0")) == 0:
+        batch_wls = _gen_batched(args.batch_systems)
 
     import torch
     import torch.distributed as dist
@@ -366,6 +518,12 @@ def main(argv=None):
                                "sample": "%d positions x all %d distributions + point charges"
                                          % (sample.size, units_per_pos)}
     env.close()
+    if batch_wls is not None:
+        out["batch"] = batch_leg(args, esp, torch, stream, flush, batch_wls)
+        del batch_wls
+    if not args.no_surrogate:
+        out["surrogate"] = surrogate_leg(args, esp, torch, stream, flush,
+                                         None if args.no_oracle else __import__("oracle"))
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

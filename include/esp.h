@@ -320,6 +320,11 @@ esp_status esp_surrogate_load(esp_ctx *ctx, const char *path, esp_surrogate **ou
 esp_status esp_surrogate_debug_step(esp_surrogate *s, const double *positions, const float *targets, int32_t n,
                                     float *params_out, float *grad_out, float *y_out);
 esp_status esp_surrogate_features(const esp_surrogate *s, float *freq_out, double *centre_inv_r_out);
+/* Test hook: the network outputs y [n] (FP32 normalised residual, before the
+ * baseline and scale are applied) of the fused tensor-core inference kernel
+ * (tcgen05) at host positions [n][3], n <= 65536.  ESP_ERR_TIMEOUT if one of
+ * the kernel's bounded waits gave up. */
+esp_status esp_surrogate_debug_net(esp_surrogate *s, const double *positions, int32_t n, float *y_out);
 
 void esp_surrogate_destroy(esp_surrogate *s);
 

@@ -5,7 +5,8 @@
 //             P_a(ux) P_b(uy) P_c(uz), a + b + c <= degree;
 //   f_theta : MLP on Fourier features (see surrogate_kernels.cu), trained on
 //             the normalised residual (V - B) / s with the library's own BF16
-//             tensor-core forward/backward kernels and Adam.
+//             tensor-core forward/backward kernels and Adam; inference runs
+//             the whole network in one tcgen05 kernel (surrogate_tc.cu).
 // Training positions follow the walker law (half) and fill the sphere
 // uniformly (half); labels come from the FP64 exact kernel.  A voxel map,
 // built from validation against the exact kernel, marks where the surrogate
@@ -75,6 +76,8 @@ struct esp_surrogate {
     DevBuf d_params, d_params_bf, d_grad, d_m, d_v, d_coef, d_powers, d_freq, d_trust;
     DevBuf d_X, d_Z, d_H, d_dZ, d_y, d_dy, d_part, d_t, d_loss;   // per-chunk activations
     DevBuf d_flag, d_pre, d_tot, d_count, d_cpos, d_cidx, d_cV, d_nfail;
+    DevBuf d_wpk, d_tcerr, d_ynet;      // packed weights, kernel status, fused-inference outputs
+    int ynet_cap = 0;
     int chunk_cap = 0, fb_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
     double last_mlp_ms = 0.0, last_total_ms = 0.0;
@@ -328,24 +331,72 @@ cudaError_t upload_vec(DevBuf &b, const std::vector<T> &v)
     return cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+TcLayout tc_layout()
+{
+    const Layout &L = layout();
+    TcLayout t;
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        t.w[l] = L.w[l];
+        t.b[l] = L.b[l];
+        t.wpk[l] = o;
+        o += size_t(kHidden) * L.in[l];
+    }
+    t.w5 = L.w5;
+    t.b5 = L.b5;
+    return t;
+}
+
+// Network outputs y (FP32, normalised residual) at n device positions, by the
+// fused tensor-core kernel.  The weights are packed from the current BF16
+// parameters on every call (416 KB, one small kernel).
+esp_status net_forward(esp_surrogate *s, const double *pos, int n, cudaStream_t st)
+{
+    cudaError_t e;
+    if (n > s->ynet_cap) {
+        if ((e = s->d_ynet.ensure(size_t(n) * sizeof(float))) != cudaSuccess)
+            return cuda_fail(e, "allocating surrogate outputs");
+        s->ynet_cap = n;
+    }
+    if ((e = s->d_wpk.ensure(tc_packed_elems() * 2)) != cudaSuccess || (e = s->d_tcerr.ensure(16)) != cudaSuccess ||
+        (e = cudaMemsetAsync(s->d_tcerr.p, 0, 4, st)) != cudaSuccess)
+        return cuda_fail(e, "allocating packed weights");
+    const TcLayout lay = tc_layout();
+    if ((e = tc_pack(static_cast<const __nv_bfloat16 *>(s->d_params_bf.p), lay,
+                     static_cast<__nv_bfloat16 *>(s->d_wpk.p), st)) != cudaSuccess ||
+        (e = tc_forward(pos, n, static_cast<const float *>(s->d_freq.p), s->centre, s->inv_r,
+                        static_cast<const __nv_bfloat16 *>(s->d_wpk.p), static_cast<const float *>(s->d_params.p), lay,
+                        static_cast<float *>(s->d_ynet.p), static_cast<int *>(s->d_tcerr.p), st)) != cudaSuccess)
+        return cuda_fail(e, "surrogate network (tensor cores)");
+    return ESP_OK;
+}
+
+// Status word of the fused kernel (read after a synchronisation point).
+esp_status net_status(esp_surrogate *s)
+{
+    if (!s->d_tcerr.p)
+        return ESP_OK;
+    int err = 0;
+    cudaError_t e = cudaMemcpy(&err, s->d_tcerr.p, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading the surrogate kernel status");
+    if (err)
+        return fail(ESP_ERR_TIMEOUT, "surrogate network kernel: a bounded wait gave up");
+    return ESP_OK;
+}
+
 // Surrogate values (baseline + network, no fallback) at n device positions.
 esp_status predict(esp_surrogate *s, const double *pos, int n, double *V, cudaStream_t st)
 {
-    const int chunk = 32768;
-    esp_status r = ensure_chunk(s, std::min(chunk, std::max(n, 1)));
+    if (n <= 0)
+        return ESP_OK;
+    esp_status r = net_forward(s, pos, n, st);
     if (r != ESP_OK)
         return r;
-    for (int o = 0; o < n; o += s->chunk_cap) {
-        const int m = std::min(s->chunk_cap, n - o);
-        if ((r = forward(s, pos + 3 * size_t(o), m, st)) != ESP_OK || (r = output_layer(s, m, nullptr, st)) != ESP_OK)
-            return r;
-        cudaError_t e = combine(pos + 3 * size_t(o), m, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p),
-                                static_cast<const int *>(s->d_powers.p), s->ncoef, s->degree,
-                                static_cast<const float *>(s->d_y.p), s->scale, V + o, st);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "surrogate combine");
-    }
-    return ESP_OK;
+    cudaError_t e = combine(pos, n, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p),
+                            static_cast<const int *>(s->d_powers.p), s->ncoef, s->degree,
+                            static_cast<const float *>(s->d_ynet.p), s->scale, V, st);
+    return e == cudaSuccess ? ESP_OK : cuda_fail(e, "surrogate combine");
 }
 
 esp_status exact_eval(esp_ctx *ctx, const double *pos, int64_t n, double *V, int precision)
@@ -567,6 +618,8 @@ esp_status train(esp_surrogate *s)
     std::vector<double> vS(cfg.n_valid), err(cfg.n_valid);
     if ((e = cudaMemcpy(vS.data(), d_vS.p, vS.size() * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "reading validation predictions");
+    if ((r = net_status(s)) != ESP_OK)
+        return r;
     double mx = 0.0, ss = 0.0, bmx = 0.0, bss = 0.0;
     {
         double P[3][kMaxDegree + 1];
@@ -629,10 +682,13 @@ esp_status sur_eval(esp_surrogate *s, const double *pos, int64_t n64, double *V,
                              static_cast<int *>(s->d_tot.p), static_cast<int *>(s->d_count.p),
                              static_cast<double *>(s->d_cpos.p), static_cast<int *>(s->d_cidx.p), st)) != cudaSuccess)
         return cuda_fail(e, "selecting fallback positions");
-    int count = 0;
+    int count = 0, tc_err = 0;
     if ((e = cudaMemcpyAsync(&count, s->d_count.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&tc_err, s->d_tcerr.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "reading the fallback count");
+    if (tc_err)
+        return fail(ESP_ERR_TIMEOUT, "surrogate network kernel: a bounded wait gave up");
     if (count > 0) {
         if ((r = esp_eval(ctx, static_cast<const double *>(s->d_cpos.p), count, static_cast<double *>(s->d_cV.p))) !=
             ESP_OK)
@@ -780,7 +836,7 @@ esp_status esp_surrogate_predict(esp_surrogate *s, const double *positions, int6
     if (r != ESP_OK)
         return r;
     cudaError_t e = cudaStreamSynchronize(s->ctx->stream);
-    return e == cudaSuccess ? ESP_OK : cuda_fail(e, "surrogate prediction");
+    return e == cudaSuccess ? net_status(s) : cuda_fail(e, "surrogate prediction");
 }
 
 esp_status esp_surrogate_info(const esp_surrogate *s, esp_surrogate_stats *stats)
@@ -829,6 +885,30 @@ esp_status esp_surrogate_debug_step(esp_surrogate *s, const double *positions, c
     if (grad_out && (e = cudaMemcpy(grad_out, s->d_grad.p, L.total * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "reading gradients");
     if (y_out && (e = cudaMemcpy(y_out, s->d_y.p, size_t(n) * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "reading outputs");
+    return ESP_OK;
+}
+
+esp_status esp_surrogate_debug_net(esp_surrogate *s, const double *positions, int32_t n, float *y_out)
+{
+    last_error().clear();
+    if (!valid_sur(s) || n <= 0 || n > 65536 || !positions || !y_out)
+        return fail(ESP_ERR_INVALID, "bad arguments");
+    DeviceGuard dg(s->ctx->device);
+    cudaStream_t st = s->ctx->stream;
+    DevBuf dp;
+    cudaError_t e;
+    if ((e = dp.ensure(size_t(n) * 24)) != cudaSuccess ||
+        (e = cudaMemcpy(dp.p, positions, size_t(n) * 24, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "staging the debug batch");
+    esp_status r = net_forward(s, static_cast<const double *>(dp.p), n, st);
+    if (r != ESP_OK)
+        return r;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "debug network");
+    if ((r = net_status(s)) != ESP_OK)
+        return r;
+    if ((e = cudaMemcpy(y_out, s->d_ynet.p, size_t(n) * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "reading outputs");
     return ESP_OK;
 }

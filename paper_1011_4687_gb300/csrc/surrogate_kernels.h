@@ -32,6 +32,21 @@ struct GemmArgs {
 };
 
 cudaError_t gemm(bool a_t, bool b_t, const GemmArgs &g, int ksplit, cudaStream_t s);
+
+// Fused tcgen05 inference (surrogate_tc.cu).  Offsets (elements) of each
+// layer's weights and biases in the flat parameter vectors, and of each
+// layer's packed weights.
+struct TcLayout {
+    size_t w[kLayers], b[kLayers], w5, b5, wpk[kLayers];
+};
+size_t tc_packed_elems();
+// Pack the BF16 weights (flat layout) into the tensor-core operand layout.
+cudaError_t tc_pack(const __nv_bfloat16 *wb, const TcLayout &lay, __nv_bfloat16 *wpk, cudaStream_t s);
+// y[i] = network output at position i (features, 4 hidden layers, output
+// layer); *err is set to 1 if a bounded wait of the kernel gave up.
+cudaError_t tc_forward(const double *pos, int n, const float *freq, const double c[3], double inv_r,
+                       const __nv_bfloat16 *wpk, const float *params, const TcLayout &lay, float *y, int *err,
+                       cudaStream_t s);
 cudaError_t features(const double *pos, int n, const float *freq, const double c[3], double inv_r,
                      __nv_bfloat16 *X, cudaStream_t s);
 // y[i] = H[i] . w + *b; with targets t: dy = 2 (y - t) / n and squared errors

@@ -1,0 +1,344 @@
+// Fused inference of the surrogate network on the 5th-generation tensor cores.
+//
+// One CTA takes 128 positions (the MMA's M) through the whole network:
+// Fourier features -> 4 x (Linear 256 + SiLU) -> Linear 1, with the
+// activations kept in shared memory as BF16 and every layer's accumulator
+// (128 x 256 FP32) in tensor memory.  Per layer, one elected thread issues
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, K = 16 per instruction) from
+// shared-memory descriptors, and commits to an mbarrier; the weights of the
+// next layer stream in with cp.async.bulk while all 8 warps read the
+// accumulator back with tcgen05.ld (warp w: lanes 32 (w % 4).., columns
+// 128 (w / 4)..), add the bias, apply SiLU and write the next layer's BF16
+// operand.  The output layer is a dot product in the last epilogue.
+//
+// Operands use the no-swizzle K-major canonical layout: 8 x 8 BF16 core
+// matrices of 128 contiguous bytes (row r of a core matrix at 16 r bytes);
+// core matrix (i, j) of an R-row operand (rows 8i.., k 8j..) at byte
+// 128 (j R/8 + i), so the stride between core matrices along M/N (SBO) is
+// 128 B and along K (LBO) is 16 R B.  Weights are packed into this layout once
+// per parameter update (pack_weights_kernel), in chunks of 64 K-columns
+// (32 KB), so each chunk is one contiguous bulk copy.
+//
+// The rounding points are those of the unfused path: features and hidden
+// activations in BF16, FP32 accumulation, FP32 bias and output weights.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "surrogate_kernels.h"
+
+namespace esp {
+namespace sur {
+
+namespace {
+
+constexpr int kRows = 128;                       // positions per CTA (MMA M)
+constexpr int kThreads = 256;                    // 8 warps
+constexpr int kChunkK = 64;                      // K columns per weight chunk
+constexpr int kChunkBytes = kHidden * kChunkK * 2; // 32 KB
+constexpr int kABytes = kRows * kHidden * 2;     // 64 KB activation operand
+constexpr int kWBytes = kHidden * kHidden * 2;   // 128 KB: one whole layer of weights
+constexpr int kTmemCols = 256;                   // FP32 accumulator columns (N)
+// bounded waits: ~1 s at a few hundred ns per suspended try_wait
+constexpr int kWaitLimit = 1 << 22;
+
+// Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5),
+// A = B = BF16 (bits 7-9, 10-12), both K-major (bits 15, 16 clear),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kHidden >> 3) << 17) |
+                            (uint32_t(kRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (M/N) byte offsets in 16-byte units, the fixed descriptor version 0b001 at
+// bits 46-48, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// one bulk copy global -> shared, completing `bytes` of transaction on bar
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+
+// byte offset of (row, k) in an R-row K-major no-swizzle operand (k % 8 == 0)
+__device__ __forceinline__ uint32_t operand_off(int row, int k, int R)
+{
+    return uint32_t(((k >> 3) * (R >> 3) + (row >> 3)) * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_tc_kernel(const double *__restrict__ pos, int n, const float *__restrict__ freq, double cx, double cy,
+                  double cz, double inv_r, const __nv_bfloat16 *__restrict__ wpk, const float *__restrict__ params,
+                  TcLayout lay, float *__restrict__ y, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem;
+    unsigned char *sW = smem + kABytes;
+    __shared__ __align__(8) uint64_t bar_w[kHidden / kChunkK];
+    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_part[2][kRows];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row0 = blockIdx.x * kRows;
+    const uint32_t aA = smem_u32(sA), aW = smem_u32(sW);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int c = 0; c < kHidden / kChunkK; ++c)
+            mbar_init(smem_u32(&bar_w[c]), 1);
+        mbar_init(smem_u32(&bar_mma), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // layer-1 weights: K = 64, one chunk
+    if (tid == 0)
+        bulk_load(aW, wpk + lay.wpk[0], kChunkBytes, smem_u32(&bar_w[0]));
+
+    // Fourier features of this CTA's rows (threads 0..127, one row each)
+    if (tid < kRows) {
+        const int i = min(row0 + tid, n - 1);
+        const float ux = float((pos[3 * i] - cx) * inv_r), uy = float((pos[3 * i + 1] - cy) * inv_r),
+                    uz = float((pos[3 * i + 2] - cz) * inv_r);
+#pragma unroll
+        for (int f0 = 0; f0 < kFreq; f0 += 8) {
+            float s[8], c[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int f = f0 + e;
+                float ph = 6.283185307179586f * (freq[3 * f] * ux + freq[3 * f + 1] * uy + freq[3 * f + 2] * uz);
+                __sincosf(ph, &s[e], &c[e]);
+            }
+            uint4 vs = make_uint4(pack_bf16x2(s[0], s[1]), pack_bf16x2(s[2], s[3]), pack_bf16x2(s[4], s[5]),
+                                  pack_bf16x2(s[6], s[7]));
+            uint4 vc = make_uint4(pack_bf16x2(c[0], c[1]), pack_bf16x2(c[2], c[3]), pack_bf16x2(c[4], c[5]),
+                                  pack_bf16x2(c[6], c[7]));
+            *reinterpret_cast<uint4 *>(sA + operand_off(tid, f0, kRows)) = vs;
+            *reinterpret_cast<uint4 *>(sA + operand_off(tid, kFreq + f0, kRows)) = vc;
+        }
+    }
+    fence_async_smem();
+    __syncthreads();
+
+    uint32_t wpar[kHidden / kChunkK] = {0, 0, 0, 0};
+    uint32_t mpar = 0;
+    const int q = warp & 3, hcol = (warp >> 2) * (kHidden / 2);
+    const int row = q * 32 + lane;
+    float part = 0.0f;
+    bool ok = true;
+    for (int l = 0; l < kLayers; ++l) {
+        const int nchunk = (l == 0 ? kFeat : kHidden) / kChunkK;
+        bool wok = true;
+        if (tid == 0) {
+            tc_fence_after();
+            for (int c = 0; c < nchunk; ++c) {
+                if (!(wok = mbar_wait(smem_u32(&bar_w[c]), wpar[c])))
+                    break;
+#pragma unroll
+                for (int ks = 0; ks < kChunkK; ks += 16) {
+                    const int k0 = c * kChunkK + ks;
+                    const uint64_t ad = smem_desc(aA + (k0 >> 3) * (kRows / 8) * 128, (kRows / 8) * 128, 128);
+                    const uint64_t bd =
+                        smem_desc(aW + c * kChunkBytes + (ks >> 3) * (kHidden / 8) * 128, (kHidden / 8) * 128, 128);
+                    mma_bf16(tmem, ad, bd, k0 > 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(smem_u32(&bar_mma)); // always: tracks whatever was issued
+        }
+        for (int c = 0; c < nchunk; ++c)
+            wpar[c] ^= 1u;
+        const bool mok = mbar_wait(smem_u32(&bar_mma), mpar);
+        mpar ^= 1u;
+        tc_fence_after();
+        if (__syncthreads_or((wok && mok) ? 0 : 1)) {
+            ok = false;
+            break;
+        }
+        // the weight buffer is free: stream in the next layer during the epilogue
+        if (tid == 0 && l + 1 < kLayers)
+            for (int c = 0; c < kHidden / kChunkK; ++c)
+                bulk_load(aW + c * kChunkBytes, wpk + lay.wpk[l + 1] + size_t(c) * (kChunkBytes / 2), kChunkBytes,
+                          smem_u32(&bar_w[c]));
+
+        const float *bias = params + lay.b[l];
+#pragma unroll 1
+        for (int cc = 0; cc < kHidden / 2; cc += 32) {
+            const int col0 = hcol + cc;
+            float v[32];
+            tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(col0), v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                v[e] = silu(v[e] + __ldg(bias + col0 + e));
+            if (l + 1 < kLayers) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    uint4 pk = make_uint4(pack_bf16x2(v[8 * m], v[8 * m + 1]), pack_bf16x2(v[8 * m + 2], v[8 * m + 3]),
+                                          pack_bf16x2(v[8 * m + 4], v[8 * m + 5]),
+                                          pack_bf16x2(v[8 * m + 6], v[8 * m + 7]));
+                    *reinterpret_cast<uint4 *>(sA + operand_off(row, col0 + 8 * m, kRows)) = pk;
+                }
+            } else {
+                const float *w5 = params + lay.w5;
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    part = fmaf(__bfloat162float(__float2bfloat16(v[e])), __ldg(w5 + col0 + e), part);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (ok) {
+        s_part[warp >> 2][row] = part;
+        __syncthreads();
+        if (tid < kRows && row0 + tid < n)
+            y[row0 + tid] = (s_part[0][tid] + s_part[1][tid]) + params[lay.b5];
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+        // let weight copies still in flight land before the CTA's shared
+        // memory is released (a completed or unused chunk returns at once)
+        for (int c = 0; c < kHidden / kChunkK; ++c)
+            mbar_wait(smem_u32(&bar_w[c]), wpar[c] ^ 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// Weights W_l [256][K] (row-major BF16, as trained) -> the K-major no-swizzle
+// layout above, in chunks of 64 K-columns.
+__global__ void pack_weights_kernel(const __nv_bfloat16 *__restrict__ wb, TcLayout lay, __nv_bfloat16 *__restrict__ wpk)
+{
+    const int l = blockIdx.y;
+    const int K = l == 0 ? kFeat : kHidden;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kHidden * K)
+        return;
+    const int nrow = e / K, k = e % K;
+    const int c = k / kChunkK, kk = k % kChunkK;
+    const size_t dst = size_t(c) * (kChunkBytes / 2) +
+                       size_t(((kk >> 3) * (kHidden >> 3) + (nrow >> 3)) * 64 + (nrow & 7) * 8 + (k & 7));
+    wpk[lay.wpk[l] + dst] = wb[lay.w[l] + size_t(nrow) * K + k];
+}
+
+} // namespace
+
+size_t tc_packed_elems() { return size_t(kHidden) * kFeat + size_t(kLayers - 1) * kHidden * kHidden; }
+
+cudaError_t tc_pack(const __nv_bfloat16 *wb, const TcLayout &lay, __nv_bfloat16 *wpk, cudaStream_t s)
+{
+    dim3 grid((kHidden * kHidden + 255) / 256, kLayers);
+    pack_weights_kernel<<<grid, 256, 0, s>>>(wb, lay, wpk);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_forward(const double *pos, int n, const float *freq, const double c[3], double inv_r,
+                       const __nv_bfloat16 *wpk, const float *params, const TcLayout &lay, float *y, int *err,
+                       cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int smem = kABytes + kWBytes;
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess)
+        return e;
+    mlp_tc_kernel<<<(n + kRows - 1) / kRows, kThreads, smem, s>>>(pos, n, freq, c[0], c[1], c[2], inv_r, wpk, params,
+                                                                   lay, y, err);
+    return cudaGetLastError();
+}
+
+} // namespace sur
+} // namespace esp

@@ -170,6 +170,8 @@ def load(build_if_missing: bool = False):
     lib.esp_surrogate_debug_step.restype = ctypes.c_int
     lib.esp_surrogate_features.argtypes = [P, P, P]
     lib.esp_surrogate_features.restype = ctypes.c_int
+    lib.esp_surrogate_debug_net.argtypes = [P, P, i32, P]
+    lib.esp_surrogate_debug_net.restype = ctypes.c_int
     lib.esp_surrogate_destroy.argtypes = [P]
     lib.esp_surrogate_destroy.restype = None
     lib.esp_set_timing.argtypes = [P, i32]
@@ -505,6 +507,13 @@ class Surrogate:
         _check(load().esp_surrogate_debug_step(self._s, pos.ctypes.data, t.ctypes.data, pos.shape[0],
                                                 params.ctypes.data, grad.ctypes.data, y.ctypes.data))
         return params, grad, y
+
+    def debug_net(self, positions: np.ndarray) -> np.ndarray:
+        """Network outputs y of the fused tensor-core inference kernel at host positions."""
+        pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+        y = np.zeros(pos.shape[0], np.float32)
+        _check(load().esp_surrogate_debug_net(self._s, pos.ctypes.data, pos.shape[0], y.ctypes.data))
+        return y
 
     def features(self):
         freq = np.zeros((32, 3), np.float32)

@@ -62,6 +62,39 @@ def trained(torch_mod):
     return wl, env, sur
 
 
+def _check_fused_network(sur, pos):
+    """The fused tcgen05 inference kernel against the CPU reference network
+    (FP64 with the kernels' BF16 rounding points) and against the unfused
+    mma.sync forward pass of the training path."""
+    y_tc = sur.debug_net(pos).astype(np.float64)
+    params, _, y_mma = sur.debug_step(pos, np.zeros(pos.shape[0], np.float32))
+    freq, c, inv_r = sur.features()
+    yr, _ = ref.forward(params.astype(np.float64), freq, c, inv_r, pos, use_bf16=True)
+    scale = max(1e-3, np.abs(yr).max())
+    assert np.all(np.isfinite(y_tc))
+    assert np.abs(y_tc - yr).max() <= 2e-2 * scale
+    assert np.abs(y_tc - y_mma).max() <= 5e-3 * scale
+    # outputs spread across the rows: a transposed or misplaced operand tile
+    # would not keep the per-position values in step with the reference
+    if pos.shape[0] > 2:
+        assert np.corrcoef(y_tc, yr)[0, 1] > 0.999
+
+
+def test_fused_network_matches_reference_untrained(torch):
+    wl = env_small()
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs)
+    with esp.Surrogate(env, n_train=2048, n_valid=512, epochs=0, degree=4) as sur:
+        # 1,000 positions: 7 full CTAs of 128 rows and a ragged last one
+        _check_fused_network(sur, qm_positions(np.random.default_rng(11), 1000))
+        _check_fused_network(sur, qm_positions(np.random.default_rng(12), 1))
+    env.close()
+
+
+def test_fused_network_matches_reference_trained(torch):
+    wl, env, sur = trained(torch)
+    _check_fused_network(sur, qm_positions(np.random.default_rng(13), 4099))
+
+
 def test_surrogate_with_fallback_meets_tolerance(torch):
     wl, env, sur = trained(torch)
     info = sur.info()

@@ -18,6 +18,8 @@ from .generate import (  # noqa: F401
     small_environment,
     realistic_environment,
     batched_environments,
+    batched_specs,
+    batched_system,
     tiny_pd_environment,
     point_cells_environment,
     seed_for_config,

@@ -453,15 +453,15 @@ def realistic_environment(seed: int = seed_for_config(2), n_atoms: int = 2000,
                     R, Z.astype(np.float64), pairs, pos, n_walkers, n_elec, np.zeros(3), meta)
 
 
-def batched_environments(seed: int = seed_for_config(3), n_sys: int = 64,
-                         pair_range=(1e4, 1e6), pos_range=(1e3, 2e5), n_elec: int = 32,
-                         distributions_per_atom: Optional[float] = None,
-                         max_atoms: Optional[int] = None) -> List[Workload]:
-    """n_sys independent environments of uneven size: distribution-count targets
-    log-uniform in pair_range, position counts log-uniform in pos_range rounded
-    to whole walkers of n_elec electrons.  Each system is a realistic environment
-    whose atom count is chosen from the target through the measured
-    distributions-per-atom ratio of that generator."""
+def batched_specs(seed: int = seed_for_config(3), n_sys: int = 64,
+                  pair_range=(1e4, 1e6), pos_range=(1e3, 2e5), n_elec: int = 32,
+                  distributions_per_atom: Optional[float] = None,
+                  max_atoms: Optional[int] = None) -> List[dict]:
+    """Per-system generator arguments of batched_environments (no environment
+    is built): distribution-count targets log-uniform in pair_range, position
+    counts log-uniform in pos_range rounded to whole walkers of n_elec
+    electrons, atom counts from the measured distributions-per-atom ratio of
+    the realistic generator."""
     rng = np.random.default_rng(seed)
     tgt = np.exp(rng.uniform(math.log(pair_range[0]), math.log(pair_range[1]), size=n_sys))
     npos = np.exp(rng.uniform(math.log(pos_range[0]), math.log(pos_range[1]), size=n_sys))
@@ -469,13 +469,29 @@ def batched_environments(seed: int = seed_for_config(3), n_sys: int = 64,
     if distributions_per_atom is None:
         probe = realistic_environment(seed=seed + 7, n_atoms=200, with_positions=False)
         distributions_per_atom = probe.meta["n_shell_pairs"] / 200.0
-    out = []
+    specs = []
     for s in range(n_sys):
         na = max(8, int(round(tgt[s] / distributions_per_atom)))
         if max_atoms is not None:
             na = min(na, max_atoms)
-        wl = realistic_environment(seed=seed * 1000 + s, n_atoms=na, n_walkers=int(nw[s]),
-                                   n_elec=n_elec)
-        wl.meta["target_distributions"] = float(tgt[s])
-        out.append(wl)
-    return out
+        specs.append({"seed": seed * 1000 + s, "n_atoms": na, "n_walkers": int(nw[s]), "n_elec": n_elec,
+                      "target_distributions": float(tgt[s])})
+    return specs
+
+
+def batched_system(spec: dict) -> Workload:
+    """One system of batched_specs (a realistic environment with its walkers)."""
+    wl = realistic_environment(seed=spec["seed"], n_atoms=spec["n_atoms"], n_walkers=spec["n_walkers"],
+                               n_elec=spec["n_elec"])
+    wl.meta["target_distributions"] = spec["target_distributions"]
+    return wl
+
+
+def batched_environments(seed: int = seed_for_config(3), n_sys: int = 64,
+                         pair_range=(1e4, 1e6), pos_range=(1e3, 2e5), n_elec: int = 32,
+                         distributions_per_atom: Optional[float] = None,
+                         max_atoms: Optional[int] = None) -> List[Workload]:
+    """n_sys independent environments of uneven size (see batched_specs); each
+    system is a realistic environment."""
+    return [batched_system(sp) for sp in batched_specs(seed, n_sys, pair_range, pos_range, n_elec,
+                                                        distributions_per_atom, max_atoms)]
