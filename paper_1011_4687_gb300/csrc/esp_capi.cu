@@ -48,6 +48,79 @@ int esp::choose_splits(const esp_ctx *c, int n, int prec)
     return std::max(s, 1);
 }
 
+int esp::plan_splits(const esp_ctx *c, int n, int prec, int max_splits, EvalArgs &a)
+{
+    const int total = std::max(1, std::min(choose_splits(c, n, prec), max_splits));
+    a.n_tiles = c->n_tiles;
+    a.n_splits = total;
+    single_group(a);
+    if (prec == 0 || c->opt.pair_splits > 0 || c->n_groups <= 1 || c->n_groups > total)
+        return total;
+    double work = 0.0;
+    for (int g = 0; g < c->n_groups; ++g)
+        work += c->grp_work[g];
+    int S[kMaxTileGroups], sum = 0;
+    for (int g = 0; g < c->n_groups; ++g) {
+        const int tiles = c->grp_tile[g + 1] - c->grp_tile[g];
+        const int want = int(std::lround(total * c->grp_work[g] / std::max(work, 1e-300)));
+        S[g] = std::max(1, std::min(want, tiles));
+        sum += S[g];
+    }
+    while (sum > total) { // give back from the group with the most splits
+        int big = 0;
+        for (int g = 1; g < c->n_groups; ++g)
+            if (S[g] > S[big])
+                big = g;
+        --S[big];
+        --sum;
+    }
+    a.n_groups = c->n_groups;
+    a.grp_split[0] = 0;
+    for (int g = 0; g < c->n_groups; ++g) {
+        a.grp_tile[g] = c->grp_tile[g];
+        a.grp_split[g + 1] = a.grp_split[g] + S[g];
+    }
+    a.grp_tile[c->n_groups] = c->grp_tile[c->n_groups];
+    a.n_splits = sum;
+    return sum;
+}
+
+void esp::set_tile_groups(esp_ctx *c)
+{
+    // FP32 operations per evaluation by L (the kernel's algorithmic count) and
+    // an FP64 point charge, for the split of the work between groups
+    static const double kCost[kMaxL + 1] = {10.0, 26.0, 52.0, 95.0, 170.0};
+    const double kPointCost = 12.0;
+    const auto &T = c->env.tiles;
+    c->n_groups = 1;
+    c->grp_tile[0] = 0;
+    c->grp_tile[1] = int(T.size());
+    c->grp_work[0] = 0.0;
+    int n = 0, prev = -1;
+    int bounds[kMaxTileGroups + 1];
+    double work[kMaxTileGroups] = {0.0};
+    for (size_t t = 0; t < T.size(); ++t) {
+        const int g = T[t].cls == kClassPoint ? 0 : 1 + (T[t].cls & 7);
+        if (g < prev || g > kMaxL + 1)
+            return; // not grouped by class: keep the plain deal
+        if (g != prev) {
+            if (n == kMaxTileGroups)
+                return;
+            bounds[n++] = int(t);
+            prev = g;
+        }
+        work[n - 1] += T[t].n * (g == 0 ? kPointCost : kCost[g - 1]);
+    }
+    if (n == 0)
+        return;
+    bounds[n] = int(T.size());
+    c->n_groups = n;
+    for (int g = 0; g <= n; ++g)
+        c->grp_tile[g] = bounds[g];
+    for (int g = 0; g < n; ++g)
+        c->grp_work[g] = work[g];
+}
+
 namespace {
 
 esp_status ensure_scratch(esp_ctx *c, int64_t n, int splits, bool host_io, int64_t n_walkers)
@@ -107,7 +180,8 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
                                      "device %d", c->device);
     const bool host_io = sp == Space::Host;
     const int prec = c->opt.precision == ESP_FP64 ? 0 : 1;
-    const int splits = choose_splits(c, int(n), prec);
+    EvalArgs a;
+    const int splits = plan_splits(c, int(n), prec, 1 << 20, a);
     esp_status st = ensure_scratch(c, n, splits, host_io, n_walkers);
     if (st != ESP_OK)
         return st;
@@ -126,10 +200,7 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
     Staged stg = staged_view(c, n);
     if ((e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s)) != cudaSuccess)
         return cuda_fail(e, "staging positions");
-    EvalArgs a;
     a.n_pos = int(n);
-    a.n_splits = splits;
-    a.n_tiles = c->n_tiles;
     a.tile_size = c->env.tile_size;
     a.pos = stg;
     a.tiles = static_cast<const TileMeta *>(c->tiles.p);
@@ -347,6 +418,7 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const 
         return fail(st, "%s", err.c_str());
     }
     c->n_tiles = int(c->env.tiles.size());
+    set_tile_groups(c);
     if (opt.flags & ESP_FLAG_HOST_ONLY) {
         c->device = -1;
         *out = c;
@@ -662,7 +734,8 @@ extern "C" esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, in
     if (st != ESP_OK)
         return st;
     const int prec = ctx->opt.precision == ESP_FP64 ? 0 : 1;
-    const int splits = std::min(choose_splits(ctx, int(n), prec), kNoallocMaxSplits);
+    EvalArgs a;
+    const int splits = plan_splits(ctx, int(n), prec, kNoallocMaxSplits, a);
     char *b = static_cast<char *>(base);
     Staged stg;
     stg.x64 = reinterpret_cast<double *>(b);
@@ -685,10 +758,7 @@ extern "C" esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, in
         if ((e = cudaMemsetAsync(partial, 0, size_t(n) * splits * sizeof(double), s)) != cudaSuccess)
             return cuda_fail(e, "clearing partial sums");
     } else {
-        EvalArgs a;
         a.n_pos = int(n);
-        a.n_splits = splits;
-        a.n_tiles = ctx->n_tiles;
         a.tile_size = ctx->env.tile_size;
         a.pos = stg;
         a.tiles = static_cast<const TileMeta *>(ctx->tiles.p);

@@ -122,6 +122,11 @@ struct esp_ctx {
     std::atomic<int> busy{0};
     int64_t device_bytes = 0;
     int n_tiles = 0;
+    // FP32C tile groups (points, L = 0..4; empty groups left out): tile ranges
+    // and estimated FP32 work, set at creation
+    int n_groups = 1;
+    int grp_tile[esp::kMaxTileGroups + 1] = {0, 0};
+    double grp_work[esp::kMaxTileGroups] = {0.0};
     int threads[2] = {128, 128};  // per precision (0 = FP64, 1 = FP32C)
     int ppt[2] = {2, 4};
     bool timing = false;
@@ -134,4 +139,10 @@ namespace esp {
 inline bool valid_ctx(const esp_ctx *c) { return c && c->magic == 0x45535021u; }
 // per-split count for n positions in precision prec (0 FP64, 1 FP32C)
 int choose_splits(const esp_ctx *c, int n, int prec);
+// Fills the deal of a's tiles (n_splits and the tile groups) for n positions,
+// with at most max_splits partial sums; returns n_splits.  FP32C deals each
+// tile group to its own splits, in proportion to the group's work.
+int plan_splits(const esp_ctx *c, int n, int prec, int max_splits, EvalArgs &a);
+// Tile groups of the built environment (at creation).
+void set_tile_groups(esp_ctx *c);
 } // namespace esp

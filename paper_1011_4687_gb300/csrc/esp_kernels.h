@@ -15,6 +15,10 @@ struct Staged {
     float *xh, *yh, *zh, *xl, *yl, *zl;
 };
 
+// FP32C tile groups: point charges, then one group per L (long- and
+// short-range tiles of that L together).
+constexpr int kMaxTileGroups = 6;
+
 struct EvalArgs {
     int n_pos;
     int n_splits;     // tiles are dealt round-robin to this many splits
@@ -28,7 +32,24 @@ struct EvalArgs {
     const double *boys64;
     double *partial;  // [n_splits][n_pos], FP64
     float near_r;     // FP32C: FP64 re-evaluation radius around a tile's bounding sphere
+    // FP32C deal by tile group: group g holds tiles [grp_tile[g], grp_tile[g+1])
+    // and takes the splits [grp_split[g], grp_split[g+1]) (grp_split[n_groups] =
+    // n_splits), so each CTA runs the code of one class.  One group over all
+    // tiles is the plain round-robin deal.
+    int n_groups;
+    int grp_tile[kMaxTileGroups + 1];
+    int grp_split[kMaxTileGroups + 1];
 };
+
+// the plain deal: every tile in one group over n_splits splits
+ESP_HD void single_group(EvalArgs &a)
+{
+    a.n_groups = 1;
+    a.grp_tile[0] = 0;
+    a.grp_tile[1] = a.n_tiles;
+    a.grp_split[0] = 0;
+    a.grp_split[1] = a.n_splits;
+}
 
 // One system of a batched evaluation (device-side table entry).
 struct SysDesc {

@@ -61,7 +61,13 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         acc64[q] = 0.0;
     }
     const float near_r = a.near_r;
-    for (int t = split; t < a.n_tiles; t += a.n_splits) {
+    // this split's group and its place among the group's splits
+    int g = 0;
+    while (g + 1 < a.n_groups && split >= a.grp_split[g + 1])
+        ++g;
+    const int g_stride = a.grp_split[g + 1] - a.grp_split[g];
+    const int g_end = a.grp_tile[g + 1];
+    for (int t = a.grp_tile[g] + (split - a.grp_split[g]); t < g_end; t += g_stride) {
         const TileMeta m = a.tiles[t];
         __syncthreads(); // previous tile fully consumed
         const bool pts = m.cls == kClassPoint;
@@ -256,6 +262,7 @@ __device__ __forceinline__ EvalArgs args_of(const SysDesc &d, const float *boys3
     a.boys64 = boys64;
     a.partial = d.partial;
     a.near_r = d.near_r;
+    single_group(a);
     return a;
 }
 
