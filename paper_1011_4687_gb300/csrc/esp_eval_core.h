@@ -110,7 +110,7 @@ ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double 
 //   offset = (P_hi - C_hi) + (P_lo - C_lo),
 // so that the fixed rounding of stored coordinates does not add up coherently
 // over the electrons of a walker; the leading coefficient carries a low word
-// for the same reason.  Terms are summed in FP32 over blocks of 16
+// for the same reason.  Terms are summed in FP32 over blocks of kSumBlock (4)
 // distributions and each block sum is added into a per-position (S, C) pair by
 // TwoSum.  Positions flagged near add nothing here (the caller evaluates the
 // tile for them in FP64).
@@ -122,7 +122,9 @@ ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double 
 // SHORT: the monopole sits in the point charge at P (M_000 is stored as 0 for
 //        the far form; the general form uses F_0 - F_0^asymptotic).
 // ---------------------------------------------------------------------------
-template <int L, int PPT, bool FAR, bool SHORT>
+// SEL: some position may be flagged near (its terms are selected away); a
+// caller that knows none is can drop the select.
+template <int L, int PPT, bool FAR, bool SHORT, bool SEL = true>
 ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[PPT][3], const float (&cl)[PPT][3],
                       const bool (&nearq)[PPT], float (&S)[PPT], float (&Cc)[PPT], const float *__restrict__ s_boys)
 {
@@ -131,68 +133,76 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
     constexpr int lo = rec32_lo(L);
     constexpr int co = FAR ? rec32_m(L) : rec32_g(L);
     constexpr int c0lo = FAR ? rec32_lo(L) + 3 : rec32_g0lo(L);
+    // one distribution j at the PPT positions, added into blk
+    auto one = [&](int j, float (&blk)[PPT]) {
+        const float *r = s_rec + j * st;
+        const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
+        const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
+        const float px = r0.x, py = r0.y, pz = r0.z, ps = r0.w;
+        const float plx = r1.x, ply = r1.y, plz = r1.z;
+        const float k0lo = FAR ? r1.w : r[c0lo];
+        float K[nh];
+        if constexpr (FAR) {
+            // the moments start 16-byte aligned: whole float4 loads
+#pragma unroll
+            for (int h = 0; h + 3 < nh; h += 4) {
+                const float4 k4 = reinterpret_cast<const float4 *>(r + co)[h / 4];
+                K[h] = k4.x;
+                K[h + 1] = k4.y;
+                K[h + 2] = k4.z;
+                K[h + 3] = k4.w;
+            }
+#pragma unroll
+            for (int h = nh - nh % 4; h < nh; ++h)
+                K[h] = r[co + h];
+        } else {
+#pragma unroll
+            for (int h = 0; h < nh; ++h)
+                K[h] = r[co + h];
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            float dx = (px - ch[q][0]) + (plx - cl[q][0]);
+            float dy = (py - ch[q][1]) + (ply - cl[q][1]);
+            float dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+            float v;
+            float F[L + 1];
+            if constexpr (FAR) {
+                boys_far<L, float>(dx * dx + dy * dy + dz * dz, F);
+                v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
+            } else if constexpr (L == 0) {
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                float T = esp_fma(ps, r2, r[rec32_pslo(L)] * r2);
+                if constexpr (SHORT)
+                    F[0] = boys_f0_short<float>(T);
+                else
+                    boys_eval<L, float>(T, s_boys, F);
+                v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
+            } else {
+                const float pslo = r[rec32_pslo(L)];
+                float x = esp_fma(ps, dx, pslo * dx), y = esp_fma(ps, dy, pslo * dy), z = esp_fma(ps, dz, pslo * dz);
+                float T = x * x + y * y + z * z;
+                boys_eval<L, float>(T, s_boys, F);
+                if constexpr (SHORT)
+                    F[0] = boys_f0_short<float>(T);
+                v = hermite_contract<L, float>(F, x, y, z, K, k0lo);
+            }
+            if constexpr (SEL)
+                blk[q] += nearq[q] ? 0.0f : v;
+            else
+                blk[q] += v;
+        }
+    };
     for (int j0 = 0; j0 < n; j0 += kSumBlock) {
         float blk[PPT];
 #pragma unroll
         for (int q = 0; q < PPT; ++q)
             blk[q] = 0.0f;
+        // (unrolling the block measured slower: more live registers at the
+        // 128-register cap of 4 positions per thread)
         const int j1 = (j0 + kSumBlock < n) ? j0 + kSumBlock : n;
-        for (int j = j0; j < j1; ++j) {
-            const float *r = s_rec + j * st;
-            const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
-            const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
-            const float px = r0.x, py = r0.y, pz = r0.z, ps = r0.w;
-            const float plx = r1.x, ply = r1.y, plz = r1.z;
-            const float k0lo = FAR ? r1.w : r[c0lo];
-            float K[nh];
-            if constexpr (FAR) {
-                // the moments start 16-byte aligned: whole float4 loads
-#pragma unroll
-                for (int h = 0; h + 3 < nh; h += 4) {
-                    const float4 k4 = reinterpret_cast<const float4 *>(r + co)[h / 4];
-                    K[h] = k4.x;
-                    K[h + 1] = k4.y;
-                    K[h + 2] = k4.z;
-                    K[h + 3] = k4.w;
-                }
-#pragma unroll
-                for (int h = nh - nh % 4; h < nh; ++h)
-                    K[h] = r[co + h];
-            } else {
-#pragma unroll
-                for (int h = 0; h < nh; ++h)
-                    K[h] = r[co + h];
-            }
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                float dx = (px - ch[q][0]) + (plx - cl[q][0]);
-                float dy = (py - ch[q][1]) + (ply - cl[q][1]);
-                float dz = (pz - ch[q][2]) + (plz - cl[q][2]);
-                float v;
-                float F[L + 1];
-                if constexpr (FAR) {
-                    boys_far<L, float>(dx * dx + dy * dy + dz * dz, F);
-                    v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
-                } else if constexpr (L == 0) {
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    float T = esp_fma(ps, r2, r[rec32_pslo(L)] * r2);
-                    if constexpr (SHORT)
-                        F[0] = boys_f0_short<float>(T);
-                    else
-                        boys_eval<L, float>(T, s_boys, F);
-                    v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
-                } else {
-                    const float pslo = r[rec32_pslo(L)];
-                    float x = esp_fma(ps, dx, pslo * dx), y = esp_fma(ps, dy, pslo * dy), z = esp_fma(ps, dz, pslo * dz);
-                    float T = x * x + y * y + z * z;
-                    boys_eval<L, float>(T, s_boys, F);
-                    if constexpr (SHORT)
-                        F[0] = boys_f0_short<float>(T);
-                    v = hermite_contract<L, float>(F, x, y, z, K, k0lo);
-                }
-                blk[q] += nearq[q] ? 0.0f : v;
-            }
-        }
+        for (int j = j0; j < j1; ++j)
+            one(j, blk);
 #pragma unroll
         for (int q = 0; q < PPT; ++q)
             two_sum_acc(S[q], Cc[q], blk[q]);

@@ -66,7 +66,10 @@ constexpr float kBoysInvStep = 8.0f;
 constexpr int kBoys32Terms = 6;          // Taylor terms (k = 0..5) of the FP32 table
 constexpr float kBoys32Tmax = 30.0f;     // asymptotic form at and above this T
 constexpr int kBoys32Rows = 241;         // T_i up to 30
-constexpr int kBoys32Row = 20;           // F_0..F_9, exp(-T_i), pad, lo words of F_0..F_4 and exp, pad
+// F_0..F_9, exp(-T_i), pad, lo words of F_0..F_4 and exp, pad x3.  The odd row
+// stride spreads the rows of a warp's gathers (one row per lane, rows a few
+// apart) over distinct shared-memory banks.
+constexpr int kBoys32Row = 21;
 constexpr int kBoys32LoCol = 12;         // low words: F_n at kBoys32LoCol + n (n <= 4), exp at + 5
 constexpr int kBoys64Terms = 9;          // Taylor terms (k = 0..8) of the FP64 table
 constexpr double kBoys64Tmax = 45.0;
@@ -152,6 +155,8 @@ ESP_HD R mul_const(R x, double k)
 {
     const R hi = R(k);
     const R lo = R(k - double(hi));
+    if (lo == R(0)) // k exact in R (folded at compile time for constant k)
+        return x * hi;
     return esp_fma(x, hi, x * lo);
 }
 

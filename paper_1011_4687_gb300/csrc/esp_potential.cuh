@@ -98,13 +98,16 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
             lane_far &= f;
         }
         const bool far = __all_sync(0xffffffffu, lane_far);
+        const bool sel = __any_sync(0xffffffffu, any_near); // warp-uniform: any term to select away
         const float *s_rec = reinterpret_cast<const float *>(s_tile4);
-#define ESP_TILE(CLS, LL, SH)                                                           \
-    case CLS:                                                                           \
-        if (far)                                                                        \
-            tile_f32c<LL, PPT, true, SH>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);     \
-        else                                                                            \
-            tile_f32c<LL, PPT, false, SH>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);    \
+#define ESP_TILE(CLS, LL, SH)                                                                   \
+    case CLS:                                                                                   \
+        if (far && !sel)                                                                        \
+            tile_f32c<LL, PPT, true, SH, false>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);      \
+        else if (far)                                                                           \
+            tile_f32c<LL, PPT, true, SH, true>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);       \
+        else                                                                                    \
+            tile_f32c<LL, PPT, false, SH, true>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);      \
         break;
         switch (m.cls) {
             ESP_TILE(0, 0, false)

@@ -988,6 +988,14 @@ esp_status esp_surrogate_load(esp_ctx *ctx, const char *path, esp_surrogate **ou
              get(s->trust.data(), s->trust.size());
         uint64_t stored = 0;
         ok = ok && std::fread(&stored, 8, 1, f) == 1 && stored == h;
+        // the evaluation kernel walks the coefficients in the fit's (a, b, c) order
+        const int D = s->degree;
+        ok = ok && s->ncoef == (D + 1) * (D + 2) * (D + 3) / 6;
+        for (int a = 0, k = 0; ok && a <= D; ++a)
+            for (int b = 0; ok && a + b <= D; ++b)
+                for (int c = 0; ok && a + b + c <= D; ++c, ++k)
+                    ok = s->powers[3 * size_t(k)] == a && s->powers[3 * size_t(k) + 1] == b &&
+                         s->powers[3 * size_t(k) + 2] == c;
     }
     std::fclose(f);
     if (!ok) {

@@ -250,12 +250,22 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, 
         wb[i] = __float2bfloat16(wi);
 }
 
-// V[i] = baseline(u) + scale * y[i] (FP64 baseline: sum_c coef[c] P_a(ux) P_b(uy) P_c(uz))
+constexpr int kMaxCoef = (kMaxDegree + 1) * (kMaxDegree + 2) * (kMaxDegree + 3) / 6;
+
+// V[i] = baseline(u) + scale * y[i] (FP64 baseline: sum_c coef[c] P_a(ux) P_b(uy) P_c(uz)).
+// The coefficients are in the fit's order (a, then b, then c ascending with
+// a + b + c <= degree; `powers` lists it), so the sum nests as
+// sum_a P_a(ux) sum_b P_b(uy) sum_c coef P_c(uz): one FMA per coefficient.
 __global__ void combine_kernel(const double *__restrict__ pos, int n, double cx, double cy, double cz,
-                               double inv_r, const double *__restrict__ coef, const int *__restrict__ powers,
-                               int ncoef, int degree, const float *__restrict__ y, double scale,
-                               double *__restrict__ V)
+                               double inv_r, const double *__restrict__ coef, int degree, const float *__restrict__ y,
+                               double scale, double *__restrict__ V)
 {
+    // coefficients in shared memory: every thread reads them in the same order
+    __shared__ double s_coef[kMaxCoef];
+    const int ncoef = (degree + 1) * (degree + 2) * (degree + 3) / 6;
+    for (int k = threadIdx.x; k < ncoef; k += blockDim.x)
+        s_coef[k] = coef[k];
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
@@ -269,8 +279,17 @@ __global__ void combine_kernel(const double *__restrict__ pos, int n, double cx,
             P[d][l + 1] = ((2 * l + 1) * u[d] * P[d][l] - l * P[d][l - 1]) / (l + 1);
     }
     double s = 0.0;
-    for (int c = 0; c < ncoef; ++c)
-        s += coef[c] * P[0][powers[3 * c]] * P[1][powers[3 * c + 1]] * P[2][powers[3 * c + 2]];
+    int k = 0;
+    for (int a = 0; a <= degree; ++a) {
+        double sa = 0.0;
+        for (int b = 0; a + b <= degree; ++b) {
+            double sb = 0.0;
+            for (int c = 0; a + b + c <= degree; ++c)
+                sb = fma(s_coef[k++], P[2][c], sb);
+            sa = fma(sb, P[1][b], sa);
+        }
+        s = fma(sa, P[0][a], s);
+    }
     V[i] = s + scale * (double)y[i];
 }
 
@@ -443,8 +462,9 @@ cudaError_t combine(const double *pos, int n, const double c[3], double inv_r, c
 {
     if (n <= 0)
         return cudaSuccess;
-    combine_kernel<<<(n + 127) / 128, 128, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, powers, ncoef, degree, y,
-                                                   scale, V);
+    (void)powers; // the kernel walks the fit's order itself (see combine_kernel)
+    (void)ncoef;
+    combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V);
     return cudaGetLastError();
 }
 

@@ -6,10 +6,11 @@
 // (128 x 256 FP32) in tensor memory.  Per layer, one elected thread issues
 // tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, K = 16 per instruction) from
 // shared-memory descriptors, and commits to an mbarrier; the weights of the
-// next layer stream in with cp.async.bulk while all 8 warps read the
+// next layer stream in with cp.async.bulk while all 16 warps read the
 // accumulator back with tcgen05.ld (warp w: lanes 32 (w % 4).., columns
-// 128 (w / 4)..), add the bias, apply SiLU and write the next layer's BF16
-// operand.  The output layer is a dot product in the last epilogue.
+// 64 (w / 4)..), add the bias (staged in shared memory), apply SiLU and write
+// the next layer's BF16 operand.  The output layer is a dot product in the
+// last epilogue.  The epilogue is latency-bound, so it runs on 16 warps.
 //
 // Operands use the no-swizzle K-major canonical layout: 8 x 8 BF16 core
 // matrices of 128 contiguous bytes (row r of a core matrix at 16 r bytes);
@@ -33,7 +34,9 @@ namespace sur {
 namespace {
 
 constexpr int kRows = 128;                       // positions per CTA (MMA M)
-constexpr int kThreads = 256;                    // 8 warps
+constexpr int kThreads = 512;                    // 16 warps: 4 lane quarters x 4 column groups
+constexpr int kColGroups = kThreads / 128;       // column groups of the epilogue
+constexpr int kGroupCols = kHidden / kColGroups; // 64 accumulator columns per warp
 constexpr int kChunkK = 64;                      // K columns per weight chunk
 constexpr int kChunkBytes = kHidden * kChunkK * 2; // 32 KB
 constexpr int kABytes = kRows * kHidden * 2;     // 64 KB activation operand
@@ -133,7 +136,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
         v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU with the fast division (the result is rounded to BF16 or multiplied
+// into an FP32 dot product; a few ulp of FP32 do not reach it)
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // byte offset of (row, k) in an R-row K-major no-swizzle operand (k % 8 == 0)
 __device__ __forceinline__ uint32_t operand_off(int row, int k, int R)
@@ -158,7 +163,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) uint64_t bar_w[kHidden / kChunkK];
     __shared__ __align__(8) uint64_t bar_mma;
     __shared__ uint32_t s_tmem;
-    __shared__ float s_part[2][kRows];
+    __shared__ float s_part[kColGroups][kRows];
+    __shared__ __align__(16) float s_bias[kLayers][kHidden];
+    __shared__ __align__(16) float s_w5[kHidden];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * kRows;
@@ -185,34 +192,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0)
         bulk_load(aW, wpk + lay.wpk[0], kChunkBytes, smem_u32(&bar_w[0]));
 
-    // Fourier features of this CTA's rows (threads 0..127, one row each)
-    if (tid < kRows) {
-        const int i = min(row0 + tid, n - 1);
+    // biases and output weights to shared memory
+    for (int i = tid; i < kLayers * kHidden; i += kThreads)
+        s_bias[i / kHidden][i % kHidden] = params[lay.b[i / kHidden] + i % kHidden];
+    for (int i = tid; i < kHidden; i += kThreads)
+        s_w5[i] = params[lay.w5 + i];
+
+    // Fourier features of this CTA's rows: row tid % 128, frequencies
+    // 8 (tid / 128) .. + 7 (sin and cos), one 16-byte store each
+    {
+        const int r = tid % kRows, f0 = 8 * (tid / kRows);
+        const int i = min(row0 + r, n - 1);
         const float ux = float((pos[3 * i] - cx) * inv_r), uy = float((pos[3 * i + 1] - cy) * inv_r),
                     uz = float((pos[3 * i + 2] - cz) * inv_r);
+        float sn[8], cs[8];
 #pragma unroll
-        for (int f0 = 0; f0 < kFreq; f0 += 8) {
-            float s[8], c[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int f = f0 + e;
-                float ph = 6.283185307179586f * (freq[3 * f] * ux + freq[3 * f + 1] * uy + freq[3 * f + 2] * uz);
-                __sincosf(ph, &s[e], &c[e]);
-            }
-            uint4 vs = make_uint4(pack_bf16x2(s[0], s[1]), pack_bf16x2(s[2], s[3]), pack_bf16x2(s[4], s[5]),
-                                  pack_bf16x2(s[6], s[7]));
-            uint4 vc = make_uint4(pack_bf16x2(c[0], c[1]), pack_bf16x2(c[2], c[3]), pack_bf16x2(c[4], c[5]),
-                                  pack_bf16x2(c[6], c[7]));
-            *reinterpret_cast<uint4 *>(sA + operand_off(tid, f0, kRows)) = vs;
-            *reinterpret_cast<uint4 *>(sA + operand_off(tid, kFreq + f0, kRows)) = vc;
+        for (int e = 0; e < 8; ++e) {
+            const int f = f0 + e;
+            float ph = 6.283185307179586f * (freq[3 * f] * ux + freq[3 * f + 1] * uy + freq[3 * f + 2] * uz);
+            __sincosf(ph, &sn[e], &cs[e]);
         }
+        const uint4 vs = make_uint4(pack_bf16x2(sn[0], sn[1]), pack_bf16x2(sn[2], sn[3]), pack_bf16x2(sn[4], sn[5]),
+                                    pack_bf16x2(sn[6], sn[7]));
+        const uint4 vc = make_uint4(pack_bf16x2(cs[0], cs[1]), pack_bf16x2(cs[2], cs[3]), pack_bf16x2(cs[4], cs[5]),
+                                    pack_bf16x2(cs[6], cs[7]));
+        *reinterpret_cast<uint4 *>(sA + operand_off(r, f0, kRows)) = vs;
+        *reinterpret_cast<uint4 *>(sA + operand_off(r, kFreq + f0, kRows)) = vc;
     }
     fence_async_smem();
     __syncthreads();
 
     uint32_t wpar[kHidden / kChunkK] = {0, 0, 0, 0};
     uint32_t mpar = 0;
-    const int q = warp & 3, hcol = (warp >> 2) * (kHidden / 2);
+    const int q = warp & 3, hcol = (warp >> 2) * kGroupCols;
     const int row = q * 32 + lane;
     float part = 0.0f;
     bool ok = true;
@@ -250,15 +262,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bulk_load(aW + c * kChunkBytes, wpk + lay.wpk[l + 1] + size_t(c) * (kChunkBytes / 2), kChunkBytes,
                           smem_u32(&bar_w[c]));
 
-        const float *bias = params + lay.b[l];
+        const float *bias = s_bias[l];
 #pragma unroll 1
-        for (int cc = 0; cc < kHidden / 2; cc += 32) {
+        for (int cc = 0; cc < kGroupCols; cc += 32) {
             const int col0 = hcol + cc;
             float v[32];
             tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(col0), v);
 #pragma unroll
             for (int e = 0; e < 32; ++e)
-                v[e] = silu(v[e] + __ldg(bias + col0 + e));
+                v[e] = silu(v[e] + bias[col0 + e]);
             if (l + 1 < kLayers) {
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
@@ -268,10 +280,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     *reinterpret_cast<uint4 *>(sA + operand_off(row, col0 + 8 * m, kRows)) = pk;
                 }
             } else {
-                const float *w5 = params + lay.w5;
+                const float *w5 = s_w5;
 #pragma unroll
                 for (int e = 0; e < 32; ++e)
-                    part = fmaf(__bfloat162float(__float2bfloat16(v[e])), __ldg(w5 + col0 + e), part);
+                    part = fmaf(__bfloat162float(__float2bfloat16(v[e])), w5[col0 + e], part);
             }
         }
         fence_async_smem();
@@ -282,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_part[warp >> 2][row] = part;
         __syncthreads();
         if (tid < kRows && row0 + tid < n)
-            y[row0 + tid] = (s_part[0][tid] + s_part[1][tid]) + params[lay.b5];
+            y[row0 + tid] = ((s_part[0][tid] + s_part[1][tid]) + (s_part[2][tid] + s_part[3][tid])) + params[lay.b5];
     } else if (tid == 0) {
         atomicExch(err, 1);
         // let weight copies still in flight land before the CTA's shared
