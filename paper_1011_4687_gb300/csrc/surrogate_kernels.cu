@@ -250,42 +250,52 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, 
         wb[i] = __float2bfloat16(wi);
 }
 
-constexpr int kMaxCoef = (kMaxDegree + 1) * (kMaxDegree + 2) * (kMaxDegree + 3) / 6;
-
 // V[i] = baseline(u) + scale * y[i] (FP64 baseline: sum_c coef[c] P_a(ux) P_b(uy) P_c(uz)).
 // The coefficients are in the fit's order (a, then b, then c ascending with
 // a + b + c <= degree; `powers` lists it), so the sum nests as
 // sum_a P_a(ux) sum_b P_b(uy) sum_c coef P_c(uz): one FMA per coefficient.
+// D > 0: the degree at compile time, so the Legendre values stay in registers;
+// D = 0: any degree (runtime loops).
+template <int D>
 __global__ void combine_kernel(const double *__restrict__ pos, int n, double cx, double cy, double cz,
-                               double inv_r, const double *__restrict__ coef, int degree, const float *__restrict__ y,
-                               double scale, double *__restrict__ V)
+                               double inv_r, const double *__restrict__ coef, int degree_rt,
+                               const float *__restrict__ y, double scale, double *__restrict__ V)
 {
-    // coefficients in shared memory: every thread reads them in the same order
-    __shared__ double s_coef[kMaxCoef];
-    const int ncoef = (degree + 1) * (degree + 2) * (degree + 3) / 6;
-    for (int k = threadIdx.x; k < ncoef; k += blockDim.x)
-        s_coef[k] = coef[k];
-    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
+    const int degree = D > 0 ? D : degree_rt;
+    constexpr int kDim = (D > 0 ? D : kMaxDegree) + 1;
     double u[3] = {(pos[3 * i] - cx) * inv_r, (pos[3 * i + 1] - cy) * inv_r, (pos[3 * i + 2] - cz) * inv_r};
-    double P[3][kMaxDegree + 1];
+    double P[3][kDim];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
         P[d][0] = 1.0;
         if (degree >= 1)
             P[d][1] = u[d];
-        for (int l = 1; l < degree; ++l)
-            P[d][l + 1] = ((2 * l + 1) * u[d] * P[d][l] - l * P[d][l - 1]) / (l + 1);
+#pragma unroll
+        for (int l = 1; l < kDim - 1; ++l)
+            if (l < degree) // Bonnet: (l + 1) P_{l+1} = (2l + 1) u P_l - l P_{l-1}
+                P[d][l + 1] = ((2 * l + 1) * u[d] * P[d][l] - l * P[d][l - 1]) * (1.0 / (l + 1));
     }
     double s = 0.0;
     int k = 0;
-    for (int a = 0; a <= degree; ++a) {
+#pragma unroll
+    for (int a = 0; a < kDim; ++a) {
+        if (a > degree)
+            break;
         double sa = 0.0;
-        for (int b = 0; a + b <= degree; ++b) {
+#pragma unroll
+        for (int b = 0; a + b < kDim; ++b) {
+            if (a + b > degree)
+                break;
             double sb = 0.0;
-            for (int c = 0; a + b + c <= degree; ++c)
-                sb = fma(s_coef[k++], P[2][c], sb);
+#pragma unroll
+            for (int c = 0; a + b + c < kDim; ++c) {
+                if (a + b + c > degree)
+                    break;
+                sb = fma(__ldg(coef + k++), P[2][c], sb);
+            }
             sa = fma(sb, P[1][b], sa);
         }
         s = fma(sa, P[0][a], s);
@@ -464,7 +474,15 @@ cudaError_t combine(const double *pos, int n, const double c[3], double inv_r, c
         return cudaSuccess;
     (void)powers; // the kernel walks the fit's order itself (see combine_kernel)
     (void)ncoef;
-    combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V);
+    const dim3 grid((n + 127) / 128), block(128);
+    switch (degree) {
+    case 4: combine_kernel<4><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
+    case 6: combine_kernel<6><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
+    case 8: combine_kernel<8><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
+    case 10: combine_kernel<10><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
+    case 12: combine_kernel<12><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
+    default: combine_kernel<0><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V);
+    }
     return cudaGetLastError();
 }
 

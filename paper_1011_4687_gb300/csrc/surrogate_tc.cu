@@ -1,6 +1,7 @@
 // Fused inference of the surrogate network on the 5th-generation tensor cores.
 //
-// One CTA takes 128 positions (the MMA's M) through the whole network:
+// One persistent CTA per SM takes tiles of 128 positions (the MMA's M), one
+// after the other, through the whole network:
 // Fourier features -> 4 x (Linear 256 + SiLU) -> Linear 1, with the
 // activations kept in shared memory as BF16 and every layer's accumulator
 // (128 x 256 FP32) in tensor memory.  Per layer, one elected thread issues
@@ -155,7 +156,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_tc_kernel(const double *__restrict__ pos, int n, const float *__restrict__ freq, double cx, double cy,
                   double cz, double inv_r, const __nv_bfloat16 *__restrict__ wpk, const float *__restrict__ params,
-                  TcLayout lay, float *__restrict__ y, int *__restrict__ err)
+                  TcLayout lay, float *__restrict__ y, int *__restrict__ err, int n_tiles)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem;
@@ -168,7 +169,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(16) float s_w5[kHidden];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row0 = blockIdx.x * kRows;
     const uint32_t aA = smem_u32(sA), aW = smem_u32(sW);
 
     if (warp == 0) {
@@ -188,114 +188,124 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    // layer-1 weights: K = 64, one chunk
-    if (tid == 0)
-        bulk_load(aW, wpk + lay.wpk[0], kChunkBytes, smem_u32(&bar_w[0]));
-
     // biases and output weights to shared memory
     for (int i = tid; i < kLayers * kHidden; i += kThreads)
         s_bias[i / kHidden][i % kHidden] = params[lay.b[i / kHidden] + i % kHidden];
     for (int i = tid; i < kHidden; i += kThreads)
         s_w5[i] = params[lay.w5 + i];
 
-    // Fourier features of this CTA's rows: row tid % 128, frequencies
-    // 8 (tid / 128) .. + 7 (sin and cos), one 16-byte store each
-    {
-        const int r = tid % kRows, f0 = 8 * (tid / kRows);
-        const int i = min(row0 + r, n - 1);
-        const float ux = float((pos[3 * i] - cx) * inv_r), uy = float((pos[3 * i + 1] - cy) * inv_r),
-                    uz = float((pos[3 * i + 2] - cz) * inv_r);
-        float sn[8], cs[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int f = f0 + e;
-            float ph = 6.283185307179586f * (freq[3 * f] * ux + freq[3 * f + 1] * uy + freq[3 * f + 2] * uz);
-            __sincosf(ph, &sn[e], &cs[e]);
-        }
-        const uint4 vs = make_uint4(pack_bf16x2(sn[0], sn[1]), pack_bf16x2(sn[2], sn[3]), pack_bf16x2(sn[4], sn[5]),
-                                    pack_bf16x2(sn[6], sn[7]));
-        const uint4 vc = make_uint4(pack_bf16x2(cs[0], cs[1]), pack_bf16x2(cs[2], cs[3]), pack_bf16x2(cs[4], cs[5]),
-                                    pack_bf16x2(cs[6], cs[7]));
-        *reinterpret_cast<uint4 *>(sA + operand_off(r, f0, kRows)) = vs;
-        *reinterpret_cast<uint4 *>(sA + operand_off(r, kFreq + f0, kRows)) = vc;
-    }
-    fence_async_smem();
-    __syncthreads();
+    // layer-1 weights of the first tile: K = 64, one chunk
+    if (tid == 0 && blockIdx.x < n_tiles)
+        bulk_load(aW, wpk + lay.wpk[0], kChunkBytes, smem_u32(&bar_w[0]));
 
     uint32_t wpar[kHidden / kChunkK] = {0, 0, 0, 0};
     uint32_t mpar = 0;
     const int q = warp & 3, hcol = (warp >> 2) * kGroupCols;
     const int row = q * 32 + lane;
-    float part = 0.0f;
     bool ok = true;
-    for (int l = 0; l < kLayers; ++l) {
-        const int nchunk = (l == 0 ? kFeat : kHidden) / kChunkK;
-        bool wok = true;
-        if (tid == 0) {
-            tc_fence_after();
-            for (int c = 0; c < nchunk; ++c) {
-                if (!(wok = mbar_wait(smem_u32(&bar_w[c]), wpar[c])))
-                    break;
+    // persistent: this CTA takes row tiles blockIdx.x, + gridDim.x, ...; the
+    // tensor memory, barriers, biases and the weight stream carry over
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int row0 = tile * kRows;
+        const bool has_next = tile + int(gridDim.x) < n_tiles;
+        // Fourier features of this CTA's rows: row tid % 128, frequencies
+        // 8 (tid / 128) .. + 7 (sin and cos), one 16-byte store each
+        {
+            const int r = tid % kRows, f0 = 8 * (tid / kRows);
+            const int i = min(row0 + r, n - 1);
+            const float ux = float((pos[3 * i] - cx) * inv_r), uy = float((pos[3 * i + 1] - cy) * inv_r),
+                        uz = float((pos[3 * i + 2] - cz) * inv_r);
+            float sn[8], cs[8];
 #pragma unroll
-                for (int ks = 0; ks < kChunkK; ks += 16) {
-                    const int k0 = c * kChunkK + ks;
-                    const uint64_t ad = smem_desc(aA + (k0 >> 3) * (kRows / 8) * 128, (kRows / 8) * 128, 128);
-                    const uint64_t bd =
-                        smem_desc(aW + c * kChunkBytes + (ks >> 3) * (kHidden / 8) * 128, (kHidden / 8) * 128, 128);
-                    mma_bf16(tmem, ad, bd, k0 > 0 ? 1u : 0u);
-                }
+            for (int e = 0; e < 8; ++e) {
+                const int f = f0 + e;
+                float ph = 6.283185307179586f * (freq[3 * f] * ux + freq[3 * f + 1] * uy + freq[3 * f + 2] * uz);
+                __sincosf(ph, &sn[e], &cs[e]);
             }
-            mma_commit(smem_u32(&bar_mma)); // always: tracks whatever was issued
-        }
-        for (int c = 0; c < nchunk; ++c)
-            wpar[c] ^= 1u;
-        const bool mok = mbar_wait(smem_u32(&bar_mma), mpar);
-        mpar ^= 1u;
-        tc_fence_after();
-        if (__syncthreads_or((wok && mok) ? 0 : 1)) {
-            ok = false;
-            break;
-        }
-        // the weight buffer is free: stream in the next layer during the epilogue
-        if (tid == 0 && l + 1 < kLayers)
-            for (int c = 0; c < kHidden / kChunkK; ++c)
-                bulk_load(aW + c * kChunkBytes, wpk + lay.wpk[l + 1] + size_t(c) * (kChunkBytes / 2), kChunkBytes,
-                          smem_u32(&bar_w[c]));
-
-        const float *bias = s_bias[l];
-#pragma unroll 1
-        for (int cc = 0; cc < kGroupCols; cc += 32) {
-            const int col0 = hcol + cc;
-            float v[32];
-            tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(col0), v);
-#pragma unroll
-            for (int e = 0; e < 32; ++e)
-                v[e] = silu(v[e] + bias[col0 + e]);
-            if (l + 1 < kLayers) {
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    uint4 pk = make_uint4(pack_bf16x2(v[8 * m], v[8 * m + 1]), pack_bf16x2(v[8 * m + 2], v[8 * m + 3]),
-                                          pack_bf16x2(v[8 * m + 4], v[8 * m + 5]),
-                                          pack_bf16x2(v[8 * m + 6], v[8 * m + 7]));
-                    *reinterpret_cast<uint4 *>(sA + operand_off(row, col0 + 8 * m, kRows)) = pk;
-                }
-            } else {
-                const float *w5 = s_w5;
-#pragma unroll
-                for (int e = 0; e < 32; ++e)
-                    part = fmaf(__bfloat162float(__float2bfloat16(v[e])), w5[col0 + e], part);
-            }
+            const uint4 vs = make_uint4(pack_bf16x2(sn[0], sn[1]), pack_bf16x2(sn[2], sn[3]), pack_bf16x2(sn[4], sn[5]),
+                                        pack_bf16x2(sn[6], sn[7]));
+            const uint4 vc = make_uint4(pack_bf16x2(cs[0], cs[1]), pack_bf16x2(cs[2], cs[3]), pack_bf16x2(cs[4], cs[5]),
+                                        pack_bf16x2(cs[6], cs[7]));
+            *reinterpret_cast<uint4 *>(sA + operand_off(r, f0, kRows)) = vs;
+            *reinterpret_cast<uint4 *>(sA + operand_off(r, kFreq + f0, kRows)) = vc;
         }
         fence_async_smem();
-        tc_fence_before();
         __syncthreads();
-    }
-    if (ok) {
-        s_part[warp >> 2][row] = part;
-        __syncthreads();
-        if (tid < kRows && row0 + tid < n)
-            y[row0 + tid] = ((s_part[0][tid] + s_part[1][tid]) + (s_part[2][tid] + s_part[3][tid])) + params[lay.b5];
-    } else if (tid == 0) {
+
+        float part = 0.0f;
+        for (int l = 0; l < kLayers; ++l) {
+            const int nchunk = (l == 0 ? kFeat : kHidden) / kChunkK;
+            bool wok = true;
+            if (tid == 0) {
+                tc_fence_after();
+                for (int c = 0; c < nchunk; ++c) {
+                    if (!(wok = mbar_wait(smem_u32(&bar_w[c]), wpar[c])))
+                        break;
+#pragma unroll
+                    for (int ks = 0; ks < kChunkK; ks += 16) {
+                        const int k0 = c * kChunkK + ks;
+                        const uint64_t ad = smem_desc(aA + (k0 >> 3) * (kRows / 8) * 128, (kRows / 8) * 128, 128);
+                        const uint64_t bd =
+                            smem_desc(aW + c * kChunkBytes + (ks >> 3) * (kHidden / 8) * 128, (kHidden / 8) * 128, 128);
+                        mma_bf16(tmem, ad, bd, k0 > 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(smem_u32(&bar_mma)); // always: tracks whatever was issued
+            }
+            for (int c = 0; c < nchunk; ++c)
+                wpar[c] ^= 1u;
+            const bool mok = mbar_wait(smem_u32(&bar_mma), mpar);
+            mpar ^= 1u;
+            tc_fence_after();
+            if (__syncthreads_or((wok && mok) ? 0 : 1)) {
+                ok = false;
+                break;
+            }
+            // the weight buffer is free: stream in the next layer (or the next
+            // tile's first layer) during the epilogue
+            if (tid == 0 && l + 1 < kLayers)
+                for (int c = 0; c < kHidden / kChunkK; ++c)
+                    bulk_load(aW + c * kChunkBytes, wpk + lay.wpk[l + 1] + size_t(c) * (kChunkBytes / 2), kChunkBytes,
+                              smem_u32(&bar_w[c]));
+            else if (tid == 0 && has_next)
+                bulk_load(aW, wpk + lay.wpk[0], kChunkBytes, smem_u32(&bar_w[0]));
+
+            const float *bias = s_bias[l];
+#pragma unroll 1
+            for (int cc = 0; cc < kGroupCols; cc += 32) {
+                const int col0 = hcol + cc;
+                float v[32];
+                tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(col0), v);
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    v[e] = silu(v[e] + bias[col0 + e]);
+                if (l + 1 < kLayers) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        uint4 pk = make_uint4(pack_bf16x2(v[8 * m], v[8 * m + 1]), pack_bf16x2(v[8 * m + 2], v[8 * m + 3]),
+                                              pack_bf16x2(v[8 * m + 4], v[8 * m + 5]),
+                                              pack_bf16x2(v[8 * m + 6], v[8 * m + 7]));
+                        *reinterpret_cast<uint4 *>(sA + operand_off(row, col0 + 8 * m, kRows)) = pk;
+                    }
+                } else {
+                    const float *w5 = s_w5;
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        part = fmaf(__bfloat162float(__float2bfloat16(v[e])), w5[col0 + e], part);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (ok) {
+            s_part[warp >> 2][row] = part;
+            __syncthreads();
+            if (tid < kRows && row0 + tid < n)
+                y[row0 + tid] = ((s_part[0][tid] + s_part[1][tid]) + (s_part[2][tid] + s_part[3][tid])) + params[lay.b5];
+        }
+    } // row tiles
+    if (!ok && tid == 0) {
         atomicExch(err, 1);
         // let weight copies still in flight land before the CTA's shared
         // memory is released (a completed or unused chunk returns at once)
@@ -347,8 +357,14 @@ cudaError_t tc_forward(const double *pos, int n, const float *freq, const double
     cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
-    mlp_tc_kernel<<<(n + kRows - 1) / kRows, kThreads, smem, s>>>(pos, n, freq, c[0], c[1], c[2], inv_r, wpk, params,
-                                                                   lay, y, err);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const int n_tiles = (n + kRows - 1) / kRows;
+    const int grid = n_tiles < sms ? n_tiles : sms; // one persistent CTA per SM
+    mlp_tc_kernel<<<grid, kThreads, smem, s>>>(pos, n, freq, c[0], c[1], c[2], inv_r, wpk, params, lay, y, err,
+                                               n_tiles);
     return cudaGetLastError();
 }
 
