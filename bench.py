@@ -309,6 +309,43 @@ def surrogate_leg(args, esp, torch, stream, flush, oracle_mod):
     return res
 
 
+def latency_leg(args, esp, torch, stream):
+    """The paper's own call pattern: its cell count (268,782 point cells +
+    36 nuclei) evaluated at one position per call (one Metropolis move), and at
+    16 per call; microseconds per call on the device (CUDA events, device
+    buffers) and through host buffers (wall clock, copies included)."""
+    from workloads import point_cells_environment
+    wl = point_cells_environment(seed=1011 * 100 + 6, n_cells=268782, n_nuclei=36, n_positions=16)
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
+    units = env.info()["n_point_charges"]
+    out = {"workload": "%d point charges (268,782 cells + 36 nuclei)" % units}
+    reps = 200
+    for npos in (1, 16):
+        pos = torch.from_numpy(wl.positions[:npos].copy()).cuda()
+        V = torch.empty(npos, dtype=torch.float64, device="cuda")
+        for _ in range(10):
+            env.eval(pos, out=V)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(reps):
+            env.eval(pos, out=V)
+        s1.record(stream)
+        s1.synchronize()
+        us = s0.elapsed_time(s1) * 1e3 / reps
+        hp = wl.positions[:npos].copy()
+        hv = np.zeros(npos)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            env.eval(hp, out=hv)
+        us_host = (time.perf_counter() - t0) * 1e6 / reps
+        out["positions_%d" % npos] = {"us_per_call": us, "us_per_call_host_buffers": us_host,
+                                      "evals_per_s": units * npos / (us * 1e-6), "launches_per_call": 3}
+    env.close()
+    return out
+
+
 def run_reference(args):
     """The oracle as it stands, on this host's cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -352,6 +389,7 @@ def main(argv=None):
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-systems leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--no-latency", action="store_true", help="skip the one-position-per-call leg")
     ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched leg")
     ap.add_argument("--walkers", type=int, default=4096,
                     help="walkers of 32 electrons per GPU (the benchmark workload is 4096; fewer only for profiling)")
@@ -521,6 +559,8 @@ def main(argv=None):
     if batch_wls is not None:
         out["batch"] = batch_leg(args, esp, torch, stream, flush, batch_wls)
         del batch_wls
+    if not args.no_latency:
+        out["few_positions_per_call"] = latency_leg(args, esp, torch, stream)
     if not args.no_surrogate:
         out["surrogate"] = surrogate_leg(args, esp, torch, stream, flush,
                                          None if args.no_oracle else __import__("oracle"))

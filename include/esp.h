@@ -155,6 +155,9 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges,
 /* V[i] = potential at positions[i] (Eq. ElectrostaticField with U_ES = -V).
  *   positions [n][3] host or device, float64, row-major
  *   V_out     [n]    same space as positions, float64
+ * Calls with at most 16 positions (the paper's one r_new per Metropolis move,
+ * Sec. III) spread the environment's entries over the GPU's threads instead
+ * of the positions and evaluate in FP64 whatever the precision setting.
  * n == 0 is a no-op.  Errors: ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_CUDA,
  * ESP_ERR_TIMEOUT, ESP_ERR_OOM. */
 esp_status esp_eval(esp_ctx *ctx, const double *positions, int64_t n, double *V_out);

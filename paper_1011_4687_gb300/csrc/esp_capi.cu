@@ -180,8 +180,10 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
                                      "device %d", c->device);
     const bool host_io = sp == Space::Host;
     const int prec = c->opt.precision == ESP_FP64 ? 0 : 1;
+    // few positions: entries spread over threads instead of positions
+    const bool small_n = n <= kSmallN && c->n_tiles > 0;
     EvalArgs a;
-    const int splits = plan_splits(c, int(n), prec, 1 << 20, a);
+    const int splits = small_n ? small_n_splits(c->n_tiles, c->num_sms) : plan_splits(c, int(n), prec, 1 << 20, a);
     esp_status st = ensure_scratch(c, n, splits, host_io, n_walkers);
     if (st != ESP_OK)
         return st;
@@ -212,16 +214,29 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
     a.near_r = float(c->opt.near_radius < 0.0 ? kDefaultNearRadius : c->opt.near_radius);
     if (c->timing && (e = cudaEventRecord(c->ev[1], s)) != cudaSuccess)
         return cuda_fail(e, "recording a timing event");
+    double *dV = (!host_io && V_out) ? V_out : static_cast<double *>(c->vout.p);
     if (c->n_tiles == 0) {
         if ((e = cudaMemsetAsync(a.partial, 0, size_t(n) * splits * sizeof(double), s)) != cudaSuccess)
             return cuda_fail(e, "clearing partial sums");
+    } else if (small_n) {
+        SmallArgs sa;
+        sa.n_pos = int(n);
+        sa.n_tiles = c->n_tiles;
+        sa.x64 = stg.x64;
+        sa.y64 = stg.y64;
+        sa.z64 = stg.z64;
+        sa.tiles = a.tiles;
+        sa.rec64 = a.rec64;
+        sa.boys64 = a.boys64;
+        sa.partial = a.partial;
+        if ((e = launch_small_n(sa, splits, dV, s)) != cudaSuccess)
+            return cuda_fail(e, "launching the few-position kernels");
     } else if ((e = launch_potential(prec, a, c->threads[prec], c->ppt[prec], s)) != cudaSuccess) {
         return cuda_fail(e, "launching the potential kernel");
     }
     if (c->timing && (e = cudaEventRecord(c->ev[2], s)) != cudaSuccess)
         return cuda_fail(e, "recording a timing event");
-    double *dV = (!host_io && V_out) ? V_out : static_cast<double *>(c->vout.p);
-    if ((e = launch_reduce(a.partial, splits, int(n), dV, s)) != cudaSuccess)
+    if (!small_n && (e = launch_reduce(a.partial, splits, int(n), dV, s)) != cudaSuccess)
         return cuda_fail(e, "launching the partial-sum reduction");
     double *dE = nullptr;
     if (E_out) {

@@ -71,8 +71,99 @@ __global__ void batch_reduce_kernel(const BatchHeader *__restrict__ hdr, const S
 }
 
 // ---------------------------------------------------------------------------
+// few positions per call (the paper's call pattern: one r_new per Metropolis
+// move).  The roles of the main kernels turn back to the paper's: threads
+// take environment entries (cells, point charges, distributions), every
+// thread evaluates its entries at all n <= kSmallN positions in FP64, the CTA
+// reduces per position in a fixed order, and CTA b writes partial[b][q].
+// Tiles are dealt round-robin to the CTAs; entries are read straight from the
+// FP64 records (each once per call).
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 64; // one thread per entry of a full tile
+
+__global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
+{
+    __shared__ double s_pos[kSmallN][3];
+    __shared__ double s_red[kSmallThreads / 32][kSmallN];
+    const int n = a.n_pos;
+    for (int i = threadIdx.x; i < n * 3; i += kSmallThreads)
+        s_pos[i / 3][i % 3] = (i % 3 == 0 ? a.x64 : i % 3 == 1 ? a.y64 : a.z64)[i / 3];
+    __syncthreads();
+    double acc[kSmallN];
+#pragma unroll
+    for (int q = 0; q < kSmallN; ++q)
+        acc[q] = 0.0;
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const TileMeta m = a.tiles[t];
+        const bool pts = m.cls == kClassPoint;
+        const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
+        for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
+            const double *r = a.rec64 + m.off64 + (size_t)j * st;
+#pragma unroll
+            for (int q = 0; q < kSmallN; ++q) {
+                if (q >= n)
+                    break;
+                if (pts) {
+                    const double dx = r[0] - s_pos[q][0], dy = r[1] - s_pos[q][1], dz = r[2] - s_pos[q][2];
+                    acc[q] += r[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
+                } else {
+                    acc[q] += tile_f64_one_any(m.cls, r, 1, s_pos[q][0], s_pos[q][1], s_pos[q][2], a.boys64);
+                }
+            }
+        }
+    }
+    // fixed-order reduction per position: warp shuffles, then the warps in order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kSmallN; ++q) {
+        if (q >= n)
+            break;
+        double v = acc[q];
+        for (int o = 16; o; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0)
+            s_red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        double v = 0.0;
+        for (int w = 0; w < kSmallThreads / 32; ++w)
+            v += s_red[w][threadIdx.x];
+        a.partial[(size_t)blockIdx.x * n + threadIdx.x] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
+// Many partials for few positions: one CTA per position, strided TwoSum per
+// thread, then a fixed-order tree over the threads' (sum, compensation) pairs.
+constexpr int kWideThreads = 256;
+
+__global__ void __launch_bounds__(kWideThreads) reduce_wide_kernel(const double *__restrict__ partial, int n_splits,
+                                                                    int n, double *__restrict__ V)
+{
+    __shared__ double s_s[kWideThreads], s_c[kWideThreads];
+    const int q = blockIdx.x, t = threadIdx.x;
+    double sum = 0.0, cmp = 0.0;
+    for (int k = t; k < n_splits; k += kWideThreads)
+        two_sum_acc(sum, cmp, partial[(size_t)k * n + q]);
+    s_s[t] = sum;
+    s_c[t] = cmp;
+    __syncthreads();
+    for (int o = kWideThreads / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            double a = s_s[t], c = s_c[t] + s_c[t + o];
+            two_sum_acc(a, c, s_s[t + o]);
+            s_s[t] = a;
+            s_c[t] = c;
+        }
+        __syncthreads();
+    }
+    if (t == 0)
+        V[q] = s_s[0] + s_c[0];
+}
+
 __global__ void reduce_kernel(const double *__restrict__ partial, int n_splits, int n, double *__restrict__ V)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,6 +265,20 @@ bool batch_shape_supported(int precision, int threads, int ppt)
 #define ESP_BSHAPE_IS(NT, PPT, PR) || (threads == NT && ppt == PPT && precision == PR)
     return false ESP_BATCH_SHAPES(ESP_BSHAPE_IS);
 #undef ESP_BSHAPE_IS
+}
+
+int small_n_splits(int n_tiles, int num_sms) { return std::max(1, std::min(n_tiles, 8 * num_sms)); }
+
+cudaError_t launch_small_n(const SmallArgs &a, int n_splits, double *V, cudaStream_t s)
+{
+    if (a.n_pos <= 0 || a.n_pos > kSmallN)
+        return cudaErrorInvalidValue;
+    small_n_kernel<<<n_splits, kSmallThreads, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    reduce_wide_kernel<<<a.n_pos, kWideThreads, 0, s>>>(a.partial, n_splits, a.n_pos, V);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s)

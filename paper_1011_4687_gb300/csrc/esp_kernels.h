@@ -86,6 +86,21 @@ size_t potential_smem_bytes(int precision, int tile_size);
 // Launch shapes compiled into the library: FP64 threads {64,128,256} x ppt {1,2};
 // FP32C (64,{2,4}), (128,{1,2,4}), (256,{1,2}).
 bool potential_shape_supported(int precision, int threads, int ppt);
+// Few positions per call (n <= kSmallN): environment entries spread over the
+// threads of n_splits CTAs, FP64 throughout, partial[split][n], then one CTA
+// per position sums the partials into V in a fixed order.
+constexpr int kSmallN = 16;
+struct SmallArgs {
+    int n_pos;
+    int n_tiles;
+    const double *x64, *y64, *z64; // staged (recentred) FP64 positions
+    const TileMeta *tiles;
+    const double *rec64;
+    const double *boys64;
+    double *partial;
+};
+int small_n_splits(int n_tiles, int num_sms);
+cudaError_t launch_small_n(const SmallArgs &a, int n_splits, double *V, cudaStream_t s);
 cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s);
 cudaError_t launch_walkers(const double *V, int n_walkers, int n_elec, double *E, cudaStream_t s);
 

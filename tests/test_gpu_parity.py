@@ -185,6 +185,37 @@ def test_point_cells(n_pos):
 
 
 # ---------------------------------------------------------------------------
+# few positions per call (<= 16: entries spread over threads, FP64 throughout)
+# against the oracle, on every class of distribution; 17 takes the main path
+# ---------------------------------------------------------------------------
+@functools.lru_cache(maxsize=None)
+def few_env():
+    return realistic_environment(seed=2718, n_atoms=40, n_walkers=1, n_elec=17)
+
+
+@pytest.mark.parametrize("n_pos", [1, 5, 16, 17])
+def test_few_positions_all_classes(n_pos):
+    wl = few_env()
+    pos = wl.positions[:n_pos]
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos)
+    for prec in ("fp64", "fp32c"):
+        with env_of(wl, prec) as env:
+            assert min(env.info()["n_by_L"]) > 0  # every L class present
+            V = env.eval(pos)
+            if prec == "fp64" or n_pos <= 16:
+                check_fp64(V, ref, "few %d %s" % (n_pos, prec))
+            else:
+                check_fp32(V, ref, "few %d %s" % (n_pos, prec))
+            # the same positions inside a larger call agree within the path's tolerance
+            Vbig = env.eval(np.concatenate([pos, wl.positions[:1].repeat(40, 0)]))[:n_pos]
+            assert np.abs(Vbig - V).max() <= (1e-10 * np.abs(ref).max() if prec == "fp64" else FP32_POINT)
+            # walker energies through the same path
+            Vw, Ew = env.eval_walkers(pos, 1, n_pos)
+            assert np.array_equal(Vw, V)
+            assert abs(Ew[0] + V.sum()) <= 1e-9 * max(1.0, np.abs(V).sum())
+
+
+# ---------------------------------------------------------------------------
 # API behaviour on the device
 # ---------------------------------------------------------------------------
 def test_host_and_device_pointers_agree_and_repeat_bitwise():
