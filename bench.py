@@ -17,6 +17,14 @@ Under torchrun each rank evaluates its own walkers against the same
 environment (weak scaling, no collective on the data path); rank 0 prints one
 JSON line.  `--impl reference` times the FP64 CPU oracle on this host's cores
 on a bounded sample of the same workload.
+
+Besides the step, the line carries (rank 0): the FP64 rate on 256 walkers,
+the accuracy of both precisions against the oracle on sampled positions, the
+oracle's own rate (cpu_baseline), the batched leg (64 uneven systems in one
+persistent graph-replayed batch vs separate calls), the few-positions-per-call
+leg (the paper's 268,782 cells, one and 16 positions per call), and the
+surrogate leg (training time, evaluation with fallback vs the exact sum,
+network-only time and errors).
 """
 from __future__ import annotations
 
@@ -131,23 +139,27 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel: str, n_pos: int):
-    """DRAM bytes of one launch at n_pos positions, from the committed ncu
-    counters: bytes for the environment (read once, L2-resident) plus bytes per
-    position; None if the kernel source changed since the capture."""
+    """DRAM bytes of one launch, from the committed ncu counters of a launch of
+    this size; None if the size differs or the kernel source changed since
+    the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
     e = t.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash() or e.get("positions") != n_pos:
         return None
-    return e["fixed_bytes"] + e["bytes_per_position"] * n_pos
+    return e["dram_bytes"]
 
 
-def build_workload(rank: int, walkers: int = 4096):
+def build_workload(rank: int, walkers: int = 4096, large: bool = False):
     from workloads import realistic_environment, seed_for_config, qm_positions
-    wl = realistic_environment(seed=seed_for_config(2))
+    if large:
+        # 20,000 atoms on a 28^3 lattice (same per-atom law), 16,384 walkers x 64 electrons
+        wl = realistic_environment(seed=seed_for_config(5), n_atoms=20000, n_walkers=16384, n_elec=64, n_side=28)
+    else:
+        wl = realistic_environment(seed=seed_for_config(2))
     if rank > 0:
         rng = np.random.default_rng(seed_for_config(2) * 1000 + rank)
         wl.positions = qm_positions(rng, wl.n_walkers * wl.n_elec)
@@ -157,11 +169,11 @@ def build_workload(rank: int, walkers: int = 4096):
     return wl
 
 
-def sample_indices(wl):
-    """Two whole walkers and the 32 positions closest to the environment."""
+def sample_indices(wl, n_walkers=2, n_outer=32):
+    """Whole walkers (the first and the last) and the positions closest to the environment."""
     r = np.linalg.norm(wl.positions, axis=1)
-    outer = np.argsort(-r)[:32]
-    ws = [0, wl.n_walkers - 1]
+    outer = np.argsort(-r)[:n_outer]
+    ws = [0, wl.n_walkers - 1][:n_walkers]
     return ws, np.concatenate([np.arange(w * wl.n_elec, (w + 1) * wl.n_elec) for w in ws] + [outer])
 
 
@@ -182,7 +194,7 @@ def _gen_batched(n_sys):
     return out
 
 
-def batch_leg(args, esp, torch, stream, flush, wls):
+def batch_leg(args, esp, torch, stream, flush, wls, oracle_mod=None):
     """Many uneven systems in one persistent, graph-replayed batch (tuned
     launch shape) against the same systems evaluated one esp_eval at a time."""
     import concurrent.futures as cf
@@ -220,6 +232,21 @@ def batch_leg(args, esp, torch, stream, flush, wls):
     k = max(1, min(args.steps, 3))
     ms_b = timed(lambda: b.eval(pos, outs), k)
     ms_s = timed(singles, k)
+    acc = None
+    if oracle_mod is not None:
+        # per-system error of the batched result against the FP64 oracle:
+        # the first and the last position of every system
+        b.eval(pos, outs)
+        torch.cuda.synchronize()
+        worst = 0.0
+        for w, o in zip(wls, outs):
+            if w.positions.shape[0] == 0:
+                continue
+            pick = np.array([0, w.positions.shape[0] - 1])
+            ref = oracle_mod.potential(w.nuclei_xyz, w.nuclei_Z, w.pairs, w.positions.reshape(-1, 3)[pick])
+            worst = max(worst, float(np.abs(o.cpu().numpy()[pick] - ref).max()))
+        acc = {"sample": "first and last position of each of the %d systems vs the FP64 oracle" % len(wls),
+               "max_point_err_ha": worst}
     res = {"workload": "%d systems, %d-%d distributions, %d-%d positions (log-uniform sizes)"
                        % (len(wls), min(units), max(units), min(int(p.shape[0]) for p in pos),
                           max(int(p.shape[0]) for p in pos)),
@@ -227,6 +254,8 @@ def batch_leg(args, esp, torch, stream, flush, wls):
            "evals_per_step": evals, "separate_evals_ms": ms_s, "speedup_vs_separate": ms_s / ms_b,
            "tuned_shape": {k2: tune[k2] for k2 in ("threads_per_block", "positions_per_thread", "split_scale")},
            "gpu_launches_per_step": 3}
+    if acc is not None:
+        res["accuracy"] = acc
     b.close()
     for e in envs:
         e.close()
@@ -393,6 +422,8 @@ def main(argv=None):
     ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched leg")
     ap.add_argument("--walkers", type=int, default=4096,
                     help="walkers of 32 electrons per GPU (the benchmark workload is 4096; fewer only for profiling)")
+    ap.add_argument("--large", action="store_true",
+                    help="the large configuration instead: 20,000 atoms, 16,384 walkers x 64 electrons")
     args = ap.parse_args(argv)
     keep_heap()
     if args.impl == "reference":
@@ -419,7 +450,9 @@ def main(argv=None):
         dist.barrier()
     esp.load()
 
-    wl = build_workload(rank, args.walkers)
+    if args.large:
+        args.walkers = 16384
+    wl = build_workload(rank, args.walkers, large=args.large)
     stream = torch.cuda.current_stream()
     env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
     info = env.info()
@@ -514,8 +547,9 @@ def main(argv=None):
     out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": ("" if args.walkers == 4096 else "REDUCED (profiling) ") +
-                                  "realistic: 2,000 atoms, cc-pVDZ-shaped primitives, %d distributions + "
+           "config": {"workload": ("large: 20,000 atoms" if args.large else
+                                   ("" if args.walkers == 4096 else "REDUCED (profiling) ") + "realistic: 2,000 atoms")
+                                  + ", cc-pVDZ-shaped primitives, %d distributions + "
                                   "%d point charges, %d positions (%d walkers x %d electrons) per GPU"
                                   % (info["n_distributions"], info["n_point_charges"], n_pos, wl.n_walkers,
                                      wl.n_elec),
@@ -536,18 +570,19 @@ def main(argv=None):
     if not args.no_oracle:
         import oracle
         oracle.build()
-        ws, sample = sample_indices(wl)
+        nws, nout = (1, 16) if args.large else (2, 32)
+        ws, sample = sample_indices(wl, nws, nout)
         t0 = time.perf_counter()
         ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions[sample])
         t_or = time.perf_counter() - t0
         Vs = V.cpu().numpy()[sample]
         Es = E.cpu().numpy()[ws]
-        Eref = oracle.walker_energies(ref[: 2 * wl.n_elec], 2, wl.n_elec)
+        Eref = oracle.walker_energies(ref[: nws * wl.n_elec], nws, wl.n_elec)
         env.set_precision("fp64")
         V64 = env.eval(torch.from_numpy(wl.positions[sample]).cuda())
         torch.cuda.synchronize()
         V64 = V64.cpu().numpy()
-        out["accuracy"] = {"sample": "2 whole walkers + 32 outermost positions",
+        out["accuracy"] = {"sample": "%d whole walker(s) + %d outermost positions" % (nws, nout),
                            "fp32c_max_point_err_ha": float(np.abs(Vs - ref).max()),
                            "fp32c_max_walker_err_ha": float(np.abs(Es - Eref).max()),
                            "fp64_max_rel_err": float(np.max(np.abs(V64 - ref) / np.maximum(np.abs(ref), 1.0)))}
@@ -557,7 +592,8 @@ def main(argv=None):
                                          % (sample.size, units_per_pos)}
     env.close()
     if batch_wls is not None:
-        out["batch"] = batch_leg(args, esp, torch, stream, flush, batch_wls)
+        out["batch"] = batch_leg(args, esp, torch, stream, flush, batch_wls,
+                                 None if args.no_oracle else __import__("oracle"))
         del batch_wls
     if not args.no_latency:
         out["few_positions_per_call"] = latency_leg(args, esp, torch, stream)
