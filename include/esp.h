@@ -103,7 +103,7 @@ typedef struct {
     double qm_center[3];           /* positions and centres are recentred here in FP64 */
     void *cuda_stream;             /* cudaStream_t for all work; NULL = the default stream */
     int32_t device;                /* CUDA device ordinal; -1 = the current device */
-    int32_t tile_size;             /* distributions per tile: 64, 128 or 256; 0 = 64 */
+    int32_t tile_size;             /* distributions per tile: 32, 64, 128 or 256; 0 = 64 */
     int32_t threads_per_block;     /* 0 = tuned default; else 64, 128 or 256 */
     int32_t positions_per_thread;  /* 0 = tuned default; FP32C shapes built: 64x{2,4},
                                       128x{1,2,4}, 256x{1,2}; FP64 uses min(this, 2) */

@@ -189,6 +189,11 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
         return st;
     cudaStream_t s = c->stream;
     cudaError_t e;
+    // FP32C with many positions: stage them in spatial order (the kernel's
+    // warp-uniform far/near votes then see compact groups of positions)
+    const bool sorted = !small_n && prec == 1 && n >= kSortMinPositions;
+    if (sorted && (e = c->sortbuf.ensure(sort_scratch_ints(int(n)) * sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "allocating the position order");
     c->timed_valid = false;
     if (c->timing && (e = cudaEventRecord(c->ev[0], s)) != cudaSuccess)
         return cuda_fail(e, "recording a timing event");
@@ -200,7 +205,11 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
         d_pos = static_cast<const double *>(c->in.p);
     }
     Staged stg = staged_view(c, n);
-    if ((e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s)) != cudaSuccess)
+    int *slot_of = nullptr, *perm = nullptr;
+    if (sorted && (e = launch_sort(d_pos, int(n), c->opt.qm_center, static_cast<int *>(c->sortbuf.p), &slot_of, &perm,
+                                   s)) != cudaSuccess)
+        return cuda_fail(e, "ordering positions");
+    if ((e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s, slot_of)) != cudaSuccess)
         return cuda_fail(e, "staging positions");
     a.n_pos = int(n);
     a.tile_size = c->env.tile_size;
@@ -236,7 +245,7 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
     }
     if (c->timing && (e = cudaEventRecord(c->ev[2], s)) != cudaSuccess)
         return cuda_fail(e, "recording a timing event");
-    if (!small_n && (e = launch_reduce(a.partial, splits, int(n), dV, s)) != cudaSuccess)
+    if (!small_n && (e = launch_reduce(a.partial, splits, int(n), dV, s, perm)) != cudaSuccess)
         return cuda_fail(e, "launching the partial-sum reduction");
     double *dE = nullptr;
     if (E_out) {
@@ -284,7 +293,7 @@ void release_all(esp_ctx *c)
             ev = nullptr;
         }
     DevBuf *bufs[] = {&c->tiles, &c->rec32, &c->rec64, &c->boys32, &c->boys64,
-                      &c->in, &c->stage, &c->partial, &c->vout, &c->eout};
+                      &c->in, &c->stage, &c->partial, &c->vout, &c->eout, &c->sortbuf};
     for (DevBuf *b : bufs)
         b->release();
 }

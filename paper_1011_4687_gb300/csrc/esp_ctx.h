@@ -118,7 +118,7 @@ struct esp_ctx {
     esp::HostEnv env;        // host copy of the tiles (kept for esp_get_info / test hook)
     bool host_copy = true;
     esp::DevBuf tiles, rec32, rec64, boys32, boys64;
-    esp::DevBuf in, stage, partial, vout, eout;
+    esp::DevBuf in, stage, partial, vout, eout, sortbuf;
     std::atomic<int> busy{0};
     int64_t device_bytes = 0;
     int n_tiles = 0;

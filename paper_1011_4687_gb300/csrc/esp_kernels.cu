@@ -15,24 +15,127 @@ namespace {
 // ---------------------------------------------------------------------------
 // staging: recentre in FP64, split into FP32 hi + lo
 // ---------------------------------------------------------------------------
+// slot_of (optional): the staged slot of position i (spatial order, below)
 __global__ void stage_kernel(const double *__restrict__ pos, int n, double cx, double cy, double cz, double q,
-                             Staged st)
+                             Staged st, const int *__restrict__ slot_of)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
     double x = pos[3 * i] - cx, y = pos[3 * i + 1] - cy, z = pos[3 * i + 2] - cz;
-    st.x64[i] = x;
-    st.y64[i] = y;
-    st.z64[i] = z;
+    const int j = slot_of ? slot_of[i] : i;
+    st.x64[j] = x;
+    st.y64[j] = y;
+    st.z64[j] = z;
     // hi words on the environment's coordinate grid q (see the pair builder)
     double xh = nearbyint(x / q) * q, yh = nearbyint(y / q) * q, zh = nearbyint(z / q) * q;
-    st.xh[i] = (float)xh;
-    st.yh[i] = (float)yh;
-    st.zh[i] = (float)zh;
-    st.xl[i] = (float)(x - xh);
-    st.yl[i] = (float)(y - yh);
-    st.zl[i] = (float)(z - zh);
+    st.xh[j] = (float)xh;
+    st.yh[j] = (float)yh;
+    st.zh[j] = (float)zh;
+    st.xl[j] = (float)(x - xh);
+    st.yl[j] = (float)(y - yh);
+    st.zl[j] = (float)(z - zh);
+}
+
+// ---------------------------------------------------------------------------
+// spatial order of the positions: a stable counting sort by the Morton code
+// of their cell in a 16^3 grid over [-8, 8]^3 bohr about the QM centre
+// (positions outside share the edge cells).  A warp's positions then sit
+// close together, so the warp-uniform far/near votes of the FP32C kernel
+// follow the tiles' distance to that small region rather than to the whole
+// QM sphere.  Deterministic: ties keep the input order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int sort_cell(const double *__restrict__ pos, int i, double cx, double cy, double cz)
+{
+    const double r[3] = {pos[3 * i] - cx, pos[3 * i + 1] - cy, pos[3 * i + 2] - cz};
+    int key = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int c = (int)floor((r[d] + kSortHalf) * (double(kSortSide) / (2.0 * kSortHalf)));
+        c = min(max(c, 0), kSortSide - 1);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            key |= ((c >> b) & 1) << (3 * b + d);
+    }
+    return key;
+}
+
+// per-block histogram of the cells of positions [b chunk, (b + 1) chunk)
+__global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const double *__restrict__ pos, int n, double cx,
+                                                                  double cy, double cz, int chunk,
+                                                                  int *__restrict__ counts)
+{
+    __shared__ int h[kSortCells];
+    for (int k = threadIdx.x; k < kSortCells; k += kSortThreads)
+        h[k] = 0;
+    __syncthreads();
+    const int beg = blockIdx.x * chunk, end = min(n, beg + chunk);
+    for (int i = beg + threadIdx.x; i < end; i += kSortThreads)
+        atomicAdd(&h[sort_cell(pos, i, cx, cy, cz)], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kSortCells; k += kSortThreads)
+        counts[(size_t)k * gridDim.x + blockIdx.x] = h[k];
+}
+
+// exclusive scan of counts[cell][block] (cell-major) in place, one CTA
+__global__ void __launch_bounds__(1024) sort_scan_kernel(int *__restrict__ counts, int m)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x, per = (m + 1023) / 1024;
+    const int beg = min(m, t * per), end = min(m, beg + per);
+    int s = 0;
+    for (int i = beg; i < end; ++i)
+        s += counts[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;
+    for (int i = beg; i < end; ++i) {
+        const int c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+}
+
+// stable scatter: slot_of[i] and perm[slot] = i
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const double *__restrict__ pos, int n, double cx,
+                                                                    double cy, double cz, int chunk,
+                                                                    const int *__restrict__ offs,
+                                                                    int *__restrict__ slot_of, int *__restrict__ perm)
+{
+    __shared__ int run[kSortCells];
+    for (int k = threadIdx.x; k < kSortCells; k += kSortThreads)
+        run[k] = offs[(size_t)k * gridDim.x + blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int beg = blockIdx.x * chunk, end = min(n, beg + chunk);
+    for (int base = beg; base < end; base += kSortThreads) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < end;
+        const int key = valid ? sort_cell(pos, i, cx, cy, cz) : -1 - lane; // unique dummy keys
+        const unsigned mask = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(mask & lt);
+        for (int w = 0; w < kSortThreads / 32; ++w) { // warps in order: ties keep the input order
+            if (warp == w) {
+                const bool leader = valid && rank == 0;
+                int b0 = leader ? run[key] : 0;
+                b0 = __shfl_sync(0xffffffffu, b0, __ffs(mask) - 1);
+                if (leader)
+                    run[key] = b0 + __popc(mask);
+                if (valid) {
+                    slot_of[i] = b0 + rank;
+                    perm[b0 + rank] = i;
+                }
+            }
+            __syncthreads();
+        }
+    }
 }
 
 __global__ void batch_stage_kernel(const BatchHeader *__restrict__ hdr, const SysDesc *__restrict__ sys)
@@ -164,7 +267,9 @@ __global__ void __launch_bounds__(kWideThreads) reduce_wide_kernel(const double 
         V[q] = s_s[0] + s_c[0];
 }
 
-__global__ void reduce_kernel(const double *__restrict__ partial, int n_splits, int n, double *__restrict__ V)
+// perm (optional): the input index of staged slot i
+__global__ void reduce_kernel(const double *__restrict__ partial, int n_splits, int n, double *__restrict__ V,
+                              const int *__restrict__ perm)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
@@ -172,7 +277,7 @@ __global__ void reduce_kernel(const double *__restrict__ partial, int n_splits, 
     double s = 0.0, c = 0.0;
     for (int k = 0; k < n_splits; ++k)
         two_sum_acc(s, c, partial[(size_t)k * n + i]);
-    V[i] = s + c;
+    V[perm ? perm[i] : i] = s + c;
 }
 
 __global__ void walker_kernel(const double *__restrict__ V, int n_walkers, int n_elec, double *__restrict__ E)
@@ -205,11 +310,34 @@ size_t potential_smem_bytes(int precision, int tile_size)
 }
 
 cudaError_t launch_stage(const double *pos_in, int n, const double center[3], double quantum, const Staged &st,
-                         cudaStream_t s)
+                         cudaStream_t s, const int *slot_of)
 {
     if (n <= 0)
         return cudaSuccess;
-    stage_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos_in, n, center[0], center[1], center[2], quantum, st);
+    stage_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos_in, n, center[0], center[1], center[2], quantum, st, slot_of);
+    return cudaGetLastError();
+}
+
+int sort_blocks(int n) { return std::max(1, std::min(256, (n + 2047) / 2048)); }
+
+size_t sort_scratch_ints(int n) { return (size_t)kSortCells * sort_blocks(n) + 2 * (size_t)n; }
+
+cudaError_t launch_sort(const double *pos_in, int n, const double center[3], int *scratch, int **slot_of, int **perm,
+                        cudaStream_t s)
+{
+    const int B = sort_blocks(n), chunk = (n + B - 1) / B;
+    int *counts = scratch;
+    *slot_of = scratch + (size_t)kSortCells * B;
+    *perm = *slot_of + n;
+    sort_count_kernel<<<B, kSortThreads, 0, s>>>(pos_in, n, center[0], center[1], center[2], chunk, counts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    sort_scan_kernel<<<1, 1024, 0, s>>>(counts, kSortCells * B);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    sort_scatter_kernel<<<B, kSortThreads, 0, s>>>(pos_in, n, center[0], center[1], center[2], chunk, counts, *slot_of,
+                                                   *perm);
     return cudaGetLastError();
 }
 
@@ -281,11 +409,11 @@ cudaError_t launch_small_n(const SmallArgs &a, int n_splits, double *V, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s)
+cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s, const int *perm)
 {
     if (n <= 0)
         return cudaSuccess;
-    reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, n_splits, n, V);
+    reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, n_splits, n, V, perm);
     return cudaGetLastError();
 }
 

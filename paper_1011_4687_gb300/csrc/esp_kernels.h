@@ -78,8 +78,21 @@ cudaError_t launch_batch(int precision, const BatchHeader *hdr, const SysDesc *s
                          int num_sms, int max_pos_total, cudaStream_t s);
 bool batch_shape_supported(int precision, int threads, int ppt);
 
+// slot_of (optional, from launch_sort): the staged slot of each input position
 cudaError_t launch_stage(const double *pos_in, int n, const double center[3], double quantum, const Staged &st,
-                         cudaStream_t s);
+                         cudaStream_t s, const int *slot_of = nullptr);
+// Spatial order of n positions (stable counting sort by the Morton code of a
+// 16^3 cell grid over [-8, 8]^3 bohr about center).  scratch holds
+// sort_scratch_ints(n) ints; on return *slot_of[i] is the slot of position i
+// and *perm[slot] its input index (both inside scratch).
+constexpr int kSortSide = 16;
+constexpr int kSortCells = kSortSide * kSortSide * kSortSide;
+constexpr int kSortThreads = 256;
+constexpr double kSortHalf = 8.0;
+constexpr int kSortMinPositions = 4096; // fewer: the order is not worth its three launches
+size_t sort_scratch_ints(int n);
+cudaError_t launch_sort(const double *pos_in, int n, const double center[3], int *scratch, int **slot_of, int **perm,
+                        cudaStream_t s);
 // precision: 0 = FP64, 1 = FP32C.  threads in {64, 128, 256}, ppt in {1, 2, 4}.
 cudaError_t launch_potential(int precision, const EvalArgs &a, int threads, int ppt, cudaStream_t s);
 size_t potential_smem_bytes(int precision, int tile_size);
@@ -101,7 +114,9 @@ struct SmallArgs {
 };
 int small_n_splits(int n_tiles, int num_sms);
 cudaError_t launch_small_n(const SmallArgs &a, int n_splits, double *V, cudaStream_t s);
-cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s);
+// perm (optional, from launch_sort): V[perm[slot]] receives the sum of slot
+cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s,
+                          const int *perm = nullptr);
 cudaError_t launch_walkers(const double *V, int n_walkers, int n_elec, double *E, cudaStream_t s);
 
 } // namespace esp

@@ -300,8 +300,8 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         return ESP_ERR_INVALID;
     }
     int tile = opt.tile_size == 0 ? 64 : opt.tile_size;
-    if (tile != 64 && tile != 128 && tile != 256) {
-        err = "tile_size must be 64, 128 or 256";
+    if (tile != 32 && tile != 64 && tile != 128 && tile != 256) {
+        err = "tile_size must be 32, 64, 128 or 256";
         return ESP_ERR_INVALID;
     }
     for (int64_t i = 0; i < n_charges; ++i) {

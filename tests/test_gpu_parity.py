@@ -216,6 +216,27 @@ def test_few_positions_all_classes(n_pos):
 
 
 # ---------------------------------------------------------------------------
+# FP32C calls of >= 4096 positions are staged in spatial order: results come
+# back in input order, repeat bitwise, and follow a permutation of the input
+# ---------------------------------------------------------------------------
+def test_spatial_order_is_invisible():
+    wl = few_env()
+    rng = np.random.default_rng(31)
+    pos = realistic_environment(seed=2718, n_atoms=40, n_walkers=160, n_elec=32).positions  # 5,120 positions
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos)
+    with env_of(wl, "fp32c") as env:
+        V = env.eval(pos)
+        check_fp32(V, ref, "ordered fp32c")
+        assert np.array_equal(env.eval(pos), V)
+        p = rng.permutation(pos.shape[0])
+        Vp = env.eval(pos[p])
+        assert np.abs(Vp - V[p]).max() <= FP32_POINT
+        Vw, Ew = env.eval_walkers(pos, 160, 32)
+        assert np.array_equal(Vw, V)
+        assert np.allclose(Ew, -V.reshape(160, 32).sum(1), rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
 # API behaviour on the device
 # ---------------------------------------------------------------------------
 def test_host_and_device_pointers_agree_and_repeat_bitwise():
