@@ -94,7 +94,8 @@ esp_status capture_graph(esp_batch *b)
     cudaError_t e3 = e2 == cudaSuccess ? cudaMemsetAsync(b->counter.p, 0, sizeof(int), s) : e2;
     const esp_ctx *c0 = b->ctxs[0];
     cudaError_t e4 = e3 == cudaSuccess
-                         ? launch_batch(b->precision, hdr, sys, static_cast<int *>(b->counter.p), 1 << 30,
+                         ? launch_batch(b->precision, hdr, sys, int(b->ctxs.size()), static_cast<int *>(b->counter.p),
+                                        1 << 30,
                                         static_cast<const float *>(c0->boys32.p),
                                         static_cast<const double *>(c0->boys64.p), b->tile_cap, b->threads, b->ppt,
                                         b->num_sms, 1 << 30, s)
@@ -152,7 +153,7 @@ esp_status batch_eval(esp_batch *b, const double *const *positions, const int64_
     cudaError_t e;
     for (int k = 0; k < ns; ++k) {
         size_t need = size_t(n[k]) * (3 * sizeof(double) + 6 * sizeof(float)) + 256 +
-                      size_t(n[k]) * size_t(splits[size_t(k)]) * sizeof(double);
+                      size_t(n[k]) * size_t(splits[size_t(k)]) * sizeof(double) + 2 * size_t(n[k]) * sizeof(int);
         if ((e = b->scratch[size_t(k)].ensure(std::max<size_t>(need, 256))) != cudaSuccess)
             return cuda_fail(e, "allocating batched scratch");
     }
@@ -189,6 +190,10 @@ esp_status batch_eval(esp_batch *b, const double *const *positions, const int64_
         d.st.zl = f + 5 * nk;
         size_t off = (size_t(nk) * (3 * sizeof(double) + 6 * sizeof(float)) + 255) / 256 * 256;
         d.partial = reinterpret_cast<double *>(base + off);
+        // FP32C systems with many positions are staged in spatial order
+        d.sorted = (b->precision == 1 && nk >= kSortMinPositions) ? 1 : 0;
+        d.slot_of = reinterpret_cast<int *>(d.partial + size_t(nk) * size_t(splits[size_t(k)]));
+        d.perm = d.slot_of + nk;
         for (int q = 0; q < 3; ++q)
             d.qm[q] = c->opt.qm_center[q];
         d.quantum = c->env.coord_quantum;

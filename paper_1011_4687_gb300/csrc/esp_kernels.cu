@@ -145,17 +145,18 @@ __global__ void batch_stage_kernel(const BatchHeader *__restrict__ hdr, const Sy
         const SysDesc &d = sys[find_sys(sys, n_sys, g, false)];
         const int i = g - d.pos_begin;
         double x = d.pos_in[3 * i] - d.qm[0], y = d.pos_in[3 * i + 1] - d.qm[1], z = d.pos_in[3 * i + 2] - d.qm[2];
-        d.st.x64[i] = x;
-        d.st.y64[i] = y;
-        d.st.z64[i] = z;
+        const int j = d.sorted ? d.slot_of[i] : i;
+        d.st.x64[j] = x;
+        d.st.y64[j] = y;
+        d.st.z64[j] = z;
         const double q = d.quantum;
         double xh = nearbyint(x / q) * q, yh = nearbyint(y / q) * q, zh = nearbyint(z / q) * q;
-        d.st.xh[i] = (float)xh;
-        d.st.yh[i] = (float)yh;
-        d.st.zh[i] = (float)zh;
-        d.st.xl[i] = (float)(x - xh);
-        d.st.yl[i] = (float)(y - yh);
-        d.st.zl[i] = (float)(z - zh);
+        d.st.xh[j] = (float)xh;
+        d.st.yh[j] = (float)yh;
+        d.st.zh[j] = (float)zh;
+        d.st.xl[j] = (float)(x - xh);
+        d.st.yl[j] = (float)(y - yh);
+        d.st.zl[j] = (float)(z - zh);
     }
 }
 
@@ -169,7 +170,76 @@ __global__ void batch_reduce_kernel(const BatchHeader *__restrict__ hdr, const S
         if (d.n_tiles > 0)
             for (int k = 0; k < d.splits; ++k)
                 two_sum_acc(s, c, d.partial[(size_t)k * d.n_pos + i]);
-        d.V_out[i] = s + c;
+        d.V_out[d.sorted ? d.perm[i] : i] = s + c;
+    }
+}
+
+// The spatial order of every sorted system of a batch, one CTA per system
+// (histogram, scan and stable scatter as above, all in shared memory).
+constexpr int kBatchSortThreads = 1024;
+
+__global__ void __launch_bounds__(kBatchSortThreads) batch_sort_kernel(const BatchHeader *__restrict__ hdr,
+                                                                       const SysDesc *__restrict__ sys)
+{
+    __shared__ int h[kSortCells];
+    __shared__ int part[kBatchSortThreads];
+    if ((int)blockIdx.x >= hdr->n_sys)
+        return;
+    const SysDesc &d = sys[blockIdx.x];
+    if (!d.sorted)
+        return;
+    const int n = d.n_pos, t = threadIdx.x;
+    for (int k = t; k < kSortCells; k += kBatchSortThreads)
+        h[k] = 0;
+    __syncthreads();
+    for (int i = t; i < n; i += kBatchSortThreads)
+        atomicAdd(&h[sort_cell(d.pos_in, i, d.qm[0], d.qm[1], d.qm[2])], 1);
+    __syncthreads();
+    // exclusive scan: each thread four consecutive cells, then the threads in order
+    constexpr int per = kSortCells / kBatchSortThreads;
+    int v[per], sum = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        v[k] = h[per * t + k];
+        sum += v[k];
+    }
+    part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < kBatchSortThreads; o <<= 1) {
+        const int x = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += x;
+        __syncthreads();
+    }
+    int run = part[t] - sum;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        h[per * t + k] = run;
+        run += v[k];
+    }
+    __syncthreads();
+    const int lane = t & 31, warp = t >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int base = 0; base < n; base += kBatchSortThreads) {
+        const int i = base + t;
+        const bool valid = i < n;
+        const int key = valid ? sort_cell(d.pos_in, i, d.qm[0], d.qm[1], d.qm[2]) : -1 - lane;
+        const unsigned mask = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(mask & lt);
+        for (int w = 0; w < kBatchSortThreads / 32; ++w) {
+            if (warp == w) {
+                const bool leader = valid && rank == 0;
+                int b0 = leader ? h[key] : 0;
+                b0 = __shfl_sync(0xffffffffu, b0, __ffs(mask) - 1);
+                if (leader)
+                    h[key] = b0 + __popc(mask);
+                if (valid) {
+                    d.slot_of[i] = b0 + rank;
+                    d.perm[b0 + rank] = i;
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -362,13 +432,17 @@ cudaError_t launch_potential(int precision, const EvalArgs &a, int threads, int 
     return cudaErrorInvalidConfiguration;
 }
 
-cudaError_t launch_batch(int precision, const BatchHeader *hdr, const SysDesc *sys, int *counter, int max_items,
-                         const float *boys32, const double *boys64, int tile_cap, int threads, int ppt,
+cudaError_t launch_batch(int precision, const BatchHeader *hdr, const SysDesc *sys, int max_sys, int *counter,
+                         int max_items, const float *boys32, const double *boys64, int tile_cap, int threads, int ppt,
                          int num_sms, int max_pos_total, cudaStream_t s)
 {
     const int sgrid = std::max(1, std::min(4 * num_sms, (max_pos_total + 255) / 256));
-    batch_stage_kernel<<<sgrid, 256, 0, s>>>(hdr, sys);
+    batch_sort_kernel<<<std::max(1, max_sys), kBatchSortThreads, 0, s>>>(hdr, sys);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    batch_stage_kernel<<<sgrid, 256, 0, s>>>(hdr, sys);
+    e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
     const size_t smem = potential_smem_bytes(precision, tile_cap);

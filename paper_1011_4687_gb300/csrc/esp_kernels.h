@@ -64,6 +64,8 @@ struct SysDesc {
     double quantum;
     int n_tiles, tile_size, n_pos, splits, blocks, item_begin, pos_begin;
     float near_r;
+    int sorted;           // stage in spatial order (slot_of / perm below are [n_pos] scratch)
+    int *slot_of, *perm;
 };
 
 struct BatchHeader {
@@ -73,7 +75,9 @@ struct BatchHeader {
 // Batched pipeline on stream s: staging, persistent potential kernel over all
 // (system, block, split) items, reduction into each system's V_out.  The
 // counter must be zero when the potential kernel starts.
-cudaError_t launch_batch(int precision, const BatchHeader *hdr, const SysDesc *sys, int *counter, int max_items,
+// max_sys: the number of systems (one spatial-order CTA each, for systems marked sorted)
+cudaError_t launch_batch(int precision, const BatchHeader *hdr, const SysDesc *sys, int max_sys, int *counter,
+                         int max_items,
                          const float *boys32, const double *boys64, int tile_cap, int threads, int ppt,
                          int num_sms, int max_pos_total, cudaStream_t s);
 bool batch_shape_supported(int precision, int threads, int ppt);

@@ -68,6 +68,30 @@ def test_batch_matches_single_evaluations(torch, prec):
         e.close()
 
 
+def test_batch_spatial_order(torch):
+    """Systems of >= 4,096 positions are staged in spatial order inside the
+    batch's graph: results return in input order and match the oracle, across
+    replays with new positions."""
+    wls = [realistic_environment(seed=510, n_atoms=60, n_walkers=130, n_elec=32),   # 4,160 positions: ordered
+           realistic_environment(seed=511, n_atoms=30, n_walkers=5, n_elec=32)]     # 160 positions: not ordered
+    stream = torch.cuda.current_stream()
+    envs = [esp.Environment(w.nuclei_xyz, w.nuclei_Z, w.pairs, stream=stream.cuda_stream) for w in wls]
+    rng = np.random.default_rng(7)
+    with esp.Batch(envs, stream=stream.cuda_stream) as b:
+        for rep in range(2):
+            host = [w.positions if rep == 0 else qm_positions(rng, w.positions.shape[0]) for w in wls]
+            outs = b.eval([torch.from_numpy(x).cuda() for x in host])
+            stream.synchronize()
+            for k, w in enumerate(wls):
+                pick = np.arange(0, host[k].shape[0], 37)
+                ref = oracle.potential(w.nuclei_xyz, w.nuclei_Z, w.pairs, host[k][pick])
+                assert np.abs(outs[k].cpu().numpy()[pick] - ref).max() <= 2e-6, (rep, k)
+                single = envs[k].eval(host[k])
+                assert np.abs(outs[k].cpu().numpy() - single).max() <= 2e-6, (rep, k)
+    for e in envs:
+        e.close()
+
+
 def test_batch_autotune_and_cache(torch, tmp_path):
     wls = systems(400)[:4]
     stream = torch.cuda.current_stream()
