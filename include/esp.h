@@ -189,7 +189,9 @@ esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_wal
  * it keeps the last call's contents: calls that overlap on the GPU (other
  * streams, other contexts, other threads) race on it, so order them on one
  * stream or synchronise between them.  The result equals esp_eval's within
- * FP32C rounding (the per-split partial count is capped at 8 here).
+ * FP32C rounding (the per-split partial count is capped at 8 here, and the
+ * positions are neither spatially ordered nor routed to the few-position
+ * path, which both need more scratch).
  * Errors: ESP_ERR_INVALID (n > ESP_NOALLOC_MAX_POSITIONS, host pointers, null
  * pointers), ESP_ERR_STATE, ESP_ERR_CUDA.  Calls no cudaMalloc or cudaFree. */
 esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, int64_t n, double *V_out);

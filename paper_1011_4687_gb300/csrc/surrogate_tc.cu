@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ float s_part[kColGroups][kRows];
     __shared__ __align__(16) float s_bias[kLayers][kHidden];
     __shared__ __align__(16) float s_w5[kHidden];
+    __shared__ float s_freq[3 * kFreq];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t aA = smem_u32(sA), aW = smem_u32(sW);
@@ -193,6 +194,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_bias[i / kHidden][i % kHidden] = params[lay.b[i / kHidden] + i % kHidden];
     for (int i = tid; i < kHidden; i += kThreads)
         s_w5[i] = params[lay.w5 + i];
+    for (int i = tid; i < 3 * kFreq; i += kThreads)
+        s_freq[i] = freq[i];
+    __syncthreads();
 
     // layer-1 weights of the first tile: K = 64, one chunk
     if (tid == 0 && blockIdx.x < n_tiles)
@@ -203,6 +207,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3, hcol = (warp >> 2) * kGroupCols;
     const int row = q * 32 + lane;
     bool ok = true;
+    // this thread's feature row (tid % 128) of the first tile; later tiles'
+    // rows are loaded during the previous tile's last layer
+    double px, py, pz;
+    {
+        const int i = min(int(blockIdx.x) * kRows + tid % kRows, n - 1);
+        px = pos[3 * i];
+        py = pos[3 * i + 1];
+        pz = pos[3 * i + 2];
+    }
     // persistent: this CTA takes row tiles blockIdx.x, + gridDim.x, ...; the
     // tensor memory, barriers, biases and the weight stream carry over
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -212,14 +225,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         // 8 (tid / 128) .. + 7 (sin and cos), one 16-byte store each
         {
             const int r = tid % kRows, f0 = 8 * (tid / kRows);
-            const int i = min(row0 + r, n - 1);
-            const float ux = float((pos[3 * i] - cx) * inv_r), uy = float((pos[3 * i + 1] - cy) * inv_r),
-                        uz = float((pos[3 * i + 2] - cz) * inv_r);
+            const float ux = float((px - cx) * inv_r), uy = float((py - cy) * inv_r), uz = float((pz - cz) * inv_r);
             float sn[8], cs[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int f = f0 + e;
-                float ph = 6.283185307179586f * (freq[3 * f] * ux + freq[3 * f + 1] * uy + freq[3 * f + 2] * uz);
+                float ph = 6.283185307179586f * (s_freq[3 * f] * ux + s_freq[3 * f + 1] * uy + s_freq[3 * f + 2] * uz);
                 __sincosf(ph, &sn[e], &cs[e]);
             }
             const uint4 vs = make_uint4(pack_bf16x2(sn[0], sn[1]), pack_bf16x2(sn[2], sn[3]), pack_bf16x2(sn[4], sn[5]),
@@ -269,6 +280,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                               smem_u32(&bar_w[c]));
             else if (tid == 0 && has_next)
                 bulk_load(aW, wpk + lay.wpk[0], kChunkBytes, smem_u32(&bar_w[0]));
+            if (l + 1 == kLayers && has_next) { // the next tile's feature row, ahead of its use
+                const int i = min((tile + int(gridDim.x)) * kRows + tid % kRows, n - 1);
+                px = pos[3 * i];
+                py = pos[3 * i + 1];
+                pz = pos[3 * i + 2];
+            }
 
             const float *bias = s_bias[l];
 #pragma unroll 1
