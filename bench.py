@@ -154,6 +154,23 @@ def profiled_traffic(kernel: str, n_pos: int):
     return e["dram_bytes"]
 
 
+def replica_positions(rank: int, n: int) -> np.ndarray:
+    """The walkers of rank > 0 under torchrun: the same law, a seed of the rank's
+    own (rank 0 keeps the workload's positions)."""
+    from workloads import seed_for_config, qm_positions
+    return qm_positions(np.random.default_rng(seed_for_config(2) * 1000 + rank), n)
+
+
+def max_over_ranks(ms: float, world: int, device: str) -> float:
+    """The slowest rank's step time (every rank returns it)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def build_workload(rank: int, walkers: int = 4096, large: bool = False):
     from workloads import realistic_environment, seed_for_config, qm_positions
     if large:
@@ -162,8 +179,7 @@ def build_workload(rank: int, walkers: int = 4096, large: bool = False):
     else:
         wl = realistic_environment(seed=seed_for_config(2))
     if rank > 0:
-        rng = np.random.default_rng(seed_for_config(2) * 1000 + rank)
-        wl.positions = qm_positions(rng, wl.n_walkers * wl.n_elec)
+        wl.positions = replica_positions(rank, wl.n_walkers * wl.n_elec)
     if walkers != wl.n_walkers:
         wl.positions = wl.positions[: walkers * wl.n_elec].copy()
         wl.n_walkers = walkers
@@ -489,10 +505,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = statistics.mean(step_ms)
-    t_rank = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    ms_max = float(t_rank.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
     value = evals_per_step * world / (ms_max * 1e-3)
     kern = statistics.mean(kern_ms)
     clocks = clk.summary()
