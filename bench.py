@@ -47,8 +47,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gaussian pair×point potential evals/s at ≤1e-5 Ha: FP64 vs FP32 vs surrogate"
 
-# FP32 operations per evaluation by total angular momentum L (see the design doc:
-# offset 3, |r|^2 3, scaled offset 3, T 1-3, Boys 2+2L, Hermite recursion and
+# FP32 operations per evaluation by total angular momentum L (offset 3,
+# |r|^2 3, scaled offset 3, T 1-3, Boys 2+2L, Hermite recursion and
 # contraction, accumulate 1).  MUFU work (one rsqrt) is not counted.
 OPS_PER_EVAL = {0: 10, 1: 26, 2: 52, 3: 95, 4: 170}
 SM_COUNT = 152

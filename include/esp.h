@@ -65,7 +65,7 @@ typedef enum {
     ESP_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in esp_last_error) */
     ESP_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out; the context stays usable */
     ESP_ERR_STATE = 5,       /* context busy in another thread, or destroyed */
-    ESP_ERR_UNSUPPORTED = 6  /* valid request this build does not handle */
+    ESP_ERR_UNSUPPORTED = 6  /* valid request the library does not handle */
 } esp_status;
 
 /* A point charge: nucleus (Z > 0) or a discretised density cell (charge -rho).
@@ -256,7 +256,7 @@ void esp_batch_destroy(esp_batch *b);
  * exact kernel stays the fallback: positions in voxels whose validation error
  * exceeded tol/2, near point charges, or picked by the online probe are
  * evaluated exactly, and a failed probe withdraws its voxel for later calls.
- * The paper has no surrogate; the exact sum it accelerates is the judge.
+ * The paper has no surrogate; the exact sum it accelerates decides its error.
  * ------------------------------------------------------------------------ */
 typedef struct esp_surrogate esp_surrogate;
 

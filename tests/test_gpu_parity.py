@@ -1,6 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (written here; the FP32C bounds are the paper's accuracy target
+restated per point and per walker):
   FP64 path : |V - V_oracle| <= 1e-10 * max(|V_oracle|, 1 Ha/e) per point;
   FP32C path: |V - V_oracle| <= 2e-6 Ha/e per point and
               |E_w - E_w,oracle| <= 1e-5 Ha per walker (E_w = -sum_e V);
