@@ -387,7 +387,7 @@ def latency_leg(args, esp, torch, stream):
             env.eval(hp, out=hv)
         us_host = (time.perf_counter() - t0) * 1e6 / reps
         out["positions_%d" % npos] = {"us_per_call": us, "us_per_call_host_buffers": us_host,
-                                      "evals_per_s": units * npos / (us * 1e-6), "launches_per_call": 3}
+                                      "evals_per_s": units * npos / (us * 1e-6), "launches_per_call": 2}
     env.close()
     return out
 

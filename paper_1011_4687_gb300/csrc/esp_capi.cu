@@ -209,7 +209,9 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
     if (sorted && (e = launch_sort(d_pos, int(n), c->opt.qm_center, static_cast<int *>(c->sortbuf.p), &slot_of, &perm,
                                    s)) != cudaSuccess)
         return cuda_fail(e, "ordering positions");
-    if ((e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s, slot_of)) != cudaSuccess)
+    // (the few-position kernel reads and recentres the positions itself)
+    if (!small_n && (e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s, slot_of)) !=
+                        cudaSuccess)
         return cuda_fail(e, "staging positions");
     a.n_pos = int(n);
     a.tile_size = c->env.tile_size;
@@ -231,9 +233,10 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
         SmallArgs sa;
         sa.n_pos = int(n);
         sa.n_tiles = c->n_tiles;
-        sa.x64 = stg.x64;
-        sa.y64 = stg.y64;
-        sa.z64 = stg.z64;
+        sa.pos_in = d_pos;
+        sa.cx = c->opt.qm_center[0];
+        sa.cy = c->opt.qm_center[1];
+        sa.cz = c->opt.qm_center[2];
         sa.tiles = a.tiles;
         sa.rec64 = a.rec64;
         sa.boys64 = a.boys64;

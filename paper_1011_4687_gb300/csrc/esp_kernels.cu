@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
     __shared__ double s_red[kSmallThreads / 32][kSmallN];
     const int n = a.n_pos;
     for (int i = threadIdx.x; i < n * 3; i += kSmallThreads)
-        s_pos[i / 3][i % 3] = (i % 3 == 0 ? a.x64 : i % 3 == 1 ? a.y64 : a.z64)[i / 3];
+        s_pos[i / 3][i % 3] = a.pos_in[i] - (i % 3 == 0 ? a.cx : i % 3 == 1 ? a.cy : a.cz);
     __syncthreads();
     double acc[kSmallN];
 #pragma unroll

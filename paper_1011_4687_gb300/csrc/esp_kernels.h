@@ -110,7 +110,8 @@ constexpr int kSmallN = 16;
 struct SmallArgs {
     int n_pos;
     int n_tiles;
-    const double *x64, *y64, *z64; // staged (recentred) FP64 positions
+    const double *pos_in;  // [n_pos][3] device positions (recentred inside the kernel)
+    double cx, cy, cz;     // QM centre
     const TileMeta *tiles;
     const double *rec64;
     const double *boys64;
