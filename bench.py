@@ -154,6 +154,14 @@ def profiled_traffic(kernel: str, n_pos: int):
     return e["dram_bytes"]
 
 
+def workload_label(wl, large: bool = False, reduced: bool = False) -> str:
+    """The workload as both arms of the benchmark name it."""
+    return (("REDUCED (profiling) " if reduced else "") +
+            ("large: 20,000 atoms" if large else "realistic: 2,000 atoms") +
+            ", cc-pVDZ-shaped primitives, local PSD density, %d positions (%d walkers x %d electrons) per GPU"
+            % (wl.n_walkers * wl.n_elec, wl.n_walkers, wl.n_elec))
+
+
 def replica_positions(rank: int, n: int) -> np.ndarray:
     """The walkers of rank > 0 under torchrun: the same law, a seed of the rank's
     own (rank 0 keeps the workload's positions)."""
@@ -414,8 +422,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "distributions": wl.meta["n_shell_pairs"],
-                       "point_charges": int(wl.nuclei_Z.size), "positions_per_step": int(sample.size)},
+            "config": {"workload": workload_label(wl), "distributions": wl.meta["n_shell_pairs"],
+                       "point_charges": int(wl.nuclei_Z.size), "oracle_positions_per_step": int(sample.size)},
             "cpu_baseline": {"value": val, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": "%d positions of the realistic workload per step (all distributions)"
                                        % sample.size},
@@ -561,12 +569,8 @@ def main(argv=None):
     out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": ("large: 20,000 atoms" if args.large else
-                                   ("" if args.walkers == 4096 else "REDUCED (profiling) ") + "realistic: 2,000 atoms")
-                                  + ", cc-pVDZ-shaped primitives, %d distributions + "
-                                  "%d point charges, %d positions (%d walkers x %d electrons) per GPU"
-                                  % (info["n_distributions"], info["n_point_charges"], n_pos, wl.n_walkers,
-                                     wl.n_elec),
+           "config": {"workload": workload_label(wl, args.large, not args.large and args.walkers != 4096),
+                      "distributions": info["n_distributions"], "point_charges": info["n_point_charges"],
                       "precision": "FP32C (FP32 pair sum, compensated; nuclei and near blocks FP64)",
                       "distributions_by_L": info["n_by_L"], "evals_per_step_per_gpu": evals_per_step,
                       "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas" if world > 1 else "single"},
