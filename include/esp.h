@@ -183,9 +183,13 @@ esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_wal
  * The scratch (staged positions and per-split partial sums) lives in one
  * file-scope device array of fixed size inside the library, about 7 MiB for
  * ESP_NOALLOC_MAX_POSITIONS positions, which every GPU that loads the library
- * holds until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture.  All calls share the array and
+ * holds until the process exits.  Under CUDA's lazy module loading (the
+ * default) the library's device module, and with it this array, is loaded on
+ * a device by the first launch or symbol lookup there: the first call on each
+ * device may therefore allocate device memory and synchronise; later calls do
+ * not.  Every call looks up the array's device address (cudaGetSymbolAddress)
+ * with the context's device current; make the first call on a device before
+ * any stream capture.  All calls share the array and
  * it keeps the last call's contents: calls that overlap on the GPU (other
  * streams, other contexts, other threads) race on it, so order them on one
  * stream or synchronise between them.  The result equals esp_eval's within

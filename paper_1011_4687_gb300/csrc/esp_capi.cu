@@ -11,7 +11,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 
@@ -702,7 +701,6 @@ constexpr int64_t kNoallocMaxPositions = ESP_NOALLOC_MAX_POSITIONS;
 constexpr int kNoallocMaxSplits = 8;
 constexpr size_t kNoallocStageBytes = size_t(kNoallocMaxPositions) * (3 * sizeof(double) + 6 * sizeof(float));
 constexpr size_t kNoallocBytes = kNoallocStageBytes + size_t(kNoallocMaxPositions) * kNoallocMaxSplits * sizeof(double);
-constexpr int kNoallocMaxDevices = 64;
 
 } // namespace
 
@@ -713,24 +711,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 namespace {
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kNoallocMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on `device` (which must be current);
-// looked up once per device.
-esp_status noalloc_scratch(int device, void **out)
+// Device address of g_noalloc_scratch on the current device.  Looked up on
+// every call (cheap): a cached address would go stale if the device's primary
+// context were reset between calls.
+esp_status noalloc_scratch(void **out)
 {
-    if (device < 0 || device >= kNoallocMaxDevices)
-        return fail(ESP_ERR_UNSUPPORTED, "device ordinal %d beyond the no-allocation table", device);
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "locating the no-allocation scratch");
-        g_noalloc_addr[device] = p;
-    }
-    *out = g_noalloc_addr[device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "locating the no-allocation scratch");
+    *out = p;
     return ESP_OK;
 }
 
@@ -756,8 +746,11 @@ extern "C" esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, in
         return fail(ESP_ERR_CUDA, "cannot select device %d", ctx->device);
     if (classify(positions, ctx->device) != Space::Device || classify(V_out, ctx->device) != Space::Device)
         return fail(ESP_ERR_INVALID, "esp_eval_noalloc takes device memory of device %d only", ctx->device);
+    // this call records no timing events: a timing query must not report the
+    // kernel times of an earlier esp_eval as this call's
+    ctx->timed_valid = false;
     void *base = nullptr;
-    esp_status st = noalloc_scratch(ctx->device, &base);
+    esp_status st = noalloc_scratch(&base);
     if (st != ESP_OK)
         return st;
     const int prec = ctx->opt.precision == ESP_FP64 ? 0 : 1;

@@ -362,3 +362,112 @@ def test_rejects_bad_pairs():
     pl = single([0, 0, 0], -1.0, [0, 0, 0], [0, 0, 0], 1.0, [0, 0, 0])
     with pytest.raises(ValueError):
         oracle.potential(np.zeros((0, 3)), np.zeros(0), pl, np.zeros((1, 3)))
+
+
+# ----------------------------------------------------------------------------
+# oracle.abs_terms: kappa = sum of |terms|, the condition of the sum.  It
+# widens the FP32C per-point bound on the synthetic p/d environments, so it is
+# pinned here by facts that do not come from its own formula.
+# ----------------------------------------------------------------------------
+def _no_pairs():
+    return PairList.empty()
+
+
+def test_abs_terms_nuclei_only_closed_form():
+    """Point charges alone: kappa = sum_beta |Z_beta| / |C - R_beta| (signs mixed)."""
+    rng = np.random.default_rng(41)
+    R = rng.uniform(-9, 9, size=(37, 3))
+    Z = rng.choice([-3.0, -1.0, 1.0, 6.0, 8.0], size=37)
+    C = rng.normal(size=(11, 3))
+    K = oracle.abs_terms(R, Z, _no_pairs(), C)
+    for i in range(C.shape[0]):
+        ref = math.fsum(abs(z) / math.sqrt(float(np.sum((C[i] - r) ** 2))) for r, z in zip(R, Z))
+        assert K[i] == pytest.approx(ref, rel=1e-14)
+
+
+@pytest.mark.parametrize("q", [-1.3, 0.4])
+def test_abs_terms_single_s_charge(q):
+    """One s-Gaussian charge: kappa = |q erf(sqrt(alpha) r) / r|, for either sign of q."""
+    rng = np.random.default_rng(43)
+    for alpha in [0.1, 2.0, 75.0]:
+        A = rng.normal(size=3)
+        for r in [0.01, 0.8, 6.0]:
+            d = rng.normal(size=3)
+            C = (A + r * d / np.linalg.norm(d))[None, :]
+            pl = single(A, alpha / 2, [0, 0, 0], A, alpha / 2, [0, 0, 0], q * (alpha / math.pi) ** 1.5)
+            K = oracle.abs_terms(np.zeros((0, 3)), np.zeros(0), pl, C)
+            assert K[0] == pytest.approx(abs(q * math.erf(math.sqrt(alpha) * r) / r), rel=1e-13)
+
+
+def test_abs_terms_single_pd_pair_vs_quadrature():
+    """One p/d pair (a term whose sign depends on the position): kappa = |quadrature potential|."""
+    pl = single([0.2, -0.1, 0.3], 0.8, [1, 0, 0], [-0.3, 0.2, 0.0], 1.1, [0, 1, 1], w=-1.7)
+    for C in ([1.1, 0.4, -0.2], [-0.6, 0.9, 0.5]):
+        C = np.array(C)
+        ref = quadrature_potential(pl, C)
+        K = oracle.abs_terms(np.zeros((0, 3)), np.zeros(0), pl, C[None, :])
+        assert K[0] == pytest.approx(abs(ref), rel=1e-8)
+
+
+def test_abs_terms_split_by_sign():
+    """Nuclei and s-charges have a position-independent sign (that of Z or q), so
+    kappa = sum over the positive sources - sum over the negative ones, each an
+    s-Gaussian closed form or a Coulomb term; and kappa >= |V|, with equality
+    when every source has one sign."""
+    wl = small_environment(n_nuclei=25, n_charges=60, n_walkers=2, n_elec=5)
+    K = oracle.abs_terms(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    V = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    q, a, S = wl.meta["s_q"], wl.meta["s_alpha"], wl.meta["s_centers"]
+    for i, C in enumerate(wl.positions):
+        terms = [z / np.linalg.norm(C - R) for R, z in zip(wl.nuclei_xyz, wl.nuclei_Z)]
+        r = np.linalg.norm(C - S, axis=1)
+        terms += [q[k] * math.erf(math.sqrt(a[k]) * r[k]) / r[k] for k in range(r.size)]
+        pos = math.fsum(t for t in terms if t > 0)
+        neg = math.fsum(t for t in terms if t < 0)
+        assert K[i] == pytest.approx(pos - neg, rel=1e-12)
+        assert K[i] >= abs(V[i]) * (1 - 1e-14)
+    # one sign only: kappa = V
+    Zp = np.abs(wl.nuclei_Z)
+    Kp = oracle.abs_terms(wl.nuclei_xyz, Zp, _no_pairs(), wl.positions)
+    Vp = oracle.potential(wl.nuclei_xyz, Zp, _no_pairs(), wl.positions)
+    assert np.allclose(Kp, Vp, rtol=1e-14, atol=0)
+
+
+def test_abs_terms_bounds_and_scaling_pd():
+    """Random p/d environments: kappa >= |V| (triangle inequality), kappa >= the
+    kappa of any subset of the sources, and kappa(c w, c Z) = |c| kappa(w, Z)."""
+    wl = tiny_pd_environment(913, n_pairs=40, n_nuclei=6, n_pos=9, exp_range=(0.2, 20.0), spread=2.0,
+                             pos_radius=2.5)
+    K = oracle.abs_terms(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    V = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    assert np.all(K >= np.abs(V) * (1 - 1e-14))
+    half = wl.pairs.subset(np.arange(len(wl.pairs) // 2))
+    Kh = oracle.abs_terms(wl.nuclei_xyz[:3], wl.nuclei_Z[:3], half, wl.positions)
+    assert np.all(K >= Kh * (1 - 1e-14))
+    # the sum of the single-pair values is kappa of the pairs
+    Kpairs = oracle.abs_terms(np.zeros((0, 3)), np.zeros(0), wl.pairs, wl.positions)
+    for i in range(3):
+        C = wl.positions[i]
+        ref = math.fsum(abs(wl.pairs.w[q] * oracle.pair_potential(wl.pairs.A[q], wl.pairs.alpha[q], wl.pairs.la[q],
+                                                                  wl.pairs.B[q], wl.pairs.beta[q], wl.pairs.lb[q], C))
+                        for q in range(len(wl.pairs)))
+        assert Kpairs[i] == pytest.approx(ref, rel=1e-13)
+    for c in (-2.5, 0.5):
+        scaled = wl.pairs.copy()
+        scaled.w = scaled.w * c
+        Ks = oracle.abs_terms(wl.nuclei_xyz, wl.nuclei_Z * c, scaled, wl.positions)
+        assert np.allclose(Ks, abs(c) * K, rtol=1e-13, atol=0)
+
+
+def test_walker_energies_compensated_vs_exact_sum():
+    """E_w = -sum_e V: against math.fsum (the correctly rounded sum, Shewchuk's
+    algorithm), on sums whose plain left-to-right evaluation loses every digit."""
+    V = np.array([1e16, 1.0, -1e16, 3.0, 2.0 ** -30, -2.0 ** -30, 0.5, 1e-3])
+    E = oracle.walker_energies(V, 2, 4)
+    assert E[0] == -math.fsum(V[:4]) == -4.0
+    assert E[1] == pytest.approx(-math.fsum(V[4:]), rel=1e-16)
+    rng = np.random.default_rng(47)
+    W = rng.normal(size=(50, 64)) * 10.0 ** rng.integers(-3, 4, size=(50, 64))
+    E = oracle.walker_energies(W.reshape(-1), 50, 64)
+    for w in range(50):
+        assert E[w] == pytest.approx(-math.fsum(W[w]), rel=1e-15, abs=1e-300)

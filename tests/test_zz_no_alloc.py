@@ -12,8 +12,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1011_4687_gb300 import build_lib, esp
-from workloads import realistic_environment
+from workloads import point_cells_environment, qm_positions, realistic_environment
 
 pytestmark = pytest.mark.gpu
 
@@ -69,3 +70,57 @@ def test_noalloc_rejects_oversize_and_host_memory():
         hv = np.zeros(8)
         st = lib.esp_eval_noalloc(env.handle, ctypes.c_void_p(hp.ctypes.data), 8, ctypes.c_void_p(hv.ctypes.data))
         assert st == esp.ESP_ERR_INVALID
+
+
+def _noalloc(lib, env, pos, V):
+    st = lib.esp_eval_noalloc(env.handle, ctypes.c_void_p(pos.data_ptr()), int(pos.shape[0]),
+                              ctypes.c_void_p(V.data_ptr()))
+    assert st == esp.ESP_OK, lib.esp_last_error().decode()
+
+
+def test_noalloc_sizes_vs_oracle_and_no_memory_growth():
+    """The largest accepted size (65,536 positions: the 8 partial-sum rows reach
+    the end of the fixed array) and 1..16 positions (which esp_eval sends to
+    another path), checked against the FP64 oracle on sampled positions; and a
+    warm call changes neither the device's free memory nor torch's."""
+    lib, torch = _lib()
+    wl = realistic_environment(seed=4244, n_atoms=60, n_walkers=2, n_elec=8)
+    stream = torch.cuda.current_stream()
+    n_max = 65536
+    pos_np = qm_positions(np.random.default_rng(4245), n_max)
+    pos = torch.from_numpy(pos_np).cuda()
+    V = torch.empty(n_max, dtype=torch.float64, device="cuda")
+    with esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c",
+                         stream=stream.cuda_stream) as env:
+        _noalloc(lib, env, pos, V)  # first call on the device: may load the module
+        stream.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        alloc0 = torch.cuda.memory_allocated()
+        _noalloc(lib, env, pos, V)
+        stream.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+        pick = np.concatenate([np.arange(8), np.arange(n_max - 8, n_max), np.arange(1000, n_max, 4099)])
+        ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos_np[pick])
+        assert np.abs(V.cpu().numpy()[pick] - ref).max() <= FP32_POINT
+        for n in (1, 5, 16):
+            Vn = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+            _noalloc(lib, env, pos[:n].contiguous(), Vn)
+            stream.synchronize()
+            assert np.abs(Vn.cpu().numpy() - ref[:n]).max() <= FP32_POINT
+
+
+def test_noalloc_point_charges_only():
+    """An environment of point charges only (the paper's cells and nuclei)."""
+    lib, torch = _lib()
+    wl = point_cells_environment(seed=4246, n_cells=3000, n_nuclei=12, n_positions=40)
+    stream = torch.cuda.current_stream()
+    pos = torch.from_numpy(wl.positions.copy()).cuda()
+    V = torch.empty(pos.shape[0], dtype=torch.float64, device="cuda")
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    with esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c",
+                         stream=stream.cuda_stream) as env:
+        for _ in range(2):
+            _noalloc(lib, env, pos, V)
+            stream.synchronize()
+            assert np.abs(V.cpu().numpy() - ref).max() <= FP32_POINT

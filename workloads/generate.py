@@ -378,10 +378,8 @@ def realistic_environment(seed: int = seed_for_config(2), n_atoms: int = 2000,
         local = np.arange(tot) - np.repeat(np.cumsum(cnt) - cnt, cnt)
         return pid, local
 
-    # Streamed in chunks of atom pairs (large numpy temporaries are slow).
-    a_keep, b_keep, d_keep, s_keep, q_keep = [], [], [], [], []
-    ap_chunk = 1500
-    for c0 in range(0, ap.shape[0], ap_chunk):
+    def _chunk(c0):
+        """Surviving component pairs of atom pairs [c0, c0 + ap_chunk)."""
         X, Y = ap[c0:c0 + ap_chunk, 0], ap[c0:c0 + ap_chunk, 1]
         nX, nY = atom_nsh[X], atom_nsh[Y]
         pid, local = _expand(nX * nY)
@@ -395,7 +393,7 @@ def realistic_environment(seed: int = seed_for_config(2), n_atoms: int = 2000,
         keep = mu * np.einsum("ij,ij->i", dAB, dAB) < 60.0
         sa, sb = sa[keep], sb[keep]
         if sa.size == 0:
-            continue
+            return None
         # shell-level screen: |D_ab| <= sqrt(D_aa D_bb) times a padded absolute-moment
         # bound that dominates every component pair of the two shells
         lA = np.repeat(sh_l[sa][:, None], 3, 1).astype(np.int32)
@@ -405,7 +403,7 @@ def realistic_environment(seed: int = seed_for_config(2), n_atoms: int = 2000,
         keep = qb * sh_dmax[sa] * sh_dmax[sb] * safety >= screen_tol
         sa, sb = sa[keep], sb[keep]
         if sa.size == 0:
-            continue
+            return None
         # component pairs of each surviving shell pair
         na, nb_ = sh_nbf[sa], sh_nbf[sb]
         spid, local = _expand(na * nb_)
@@ -419,15 +417,27 @@ def realistic_environment(seed: int = seed_for_config(2), n_atoms: int = 2000,
         keep = np.sqrt(Daa[a_bf] * Daa[b_bf]) * qabs * safety >= screen_tol
         a_bf, b_bf = a_bf[keep], b_bf[keep]
         if a_bf.size == 0:
-            continue
+            return None
         D = np.asarray(Bm[a_bf].multiply(Bm[b_bf]).sum(axis=1)).ravel()
         ea, eb = sh_exp[bf_shell[a_bf]], sh_exp[bf_shell[b_bf]]
         S = product_overlap(R[bf_atom[a_bf]], ea, bf_lmn[a_bf], R[bf_atom[b_bf]], eb, bf_lmn[b_bf])
-        a_keep.append(a_bf)
-        b_keep.append(b_bf)
-        d_keep.append(D)
-        s_keep.append(S)
-        q_keep.append(qabs[keep])
+        return a_bf, b_bf, D, S, qabs[keep]
+
+    # Streamed in chunks of atom pairs (large numpy temporaries are slow); the
+    # chunks run on threads (numpy and scipy.sparse release the GIL in their
+    # array loops) and are joined in chunk order, so the result does not depend
+    # on the thread count.
+    import concurrent.futures as cf
+    import os
+    ap_chunk = 1500
+    starts = range(0, ap.shape[0], ap_chunk)
+    n_thr = max(1, min(16, os.cpu_count() or 1, len(starts)))
+    if n_thr > 1:
+        with cf.ThreadPoolExecutor(max_workers=n_thr) as ex:
+            parts = [r for r in ex.map(_chunk, starts) if r is not None]
+    else:
+        parts = [r for r in map(_chunk, starts) if r is not None]
+    a_keep, b_keep, d_keep, s_keep, q_keep = (list(x) for x in zip(*parts))
     a = np.concatenate(a_keep)
     b = np.concatenate(b_keep)
     Dab = np.concatenate(d_keep)
