@@ -3,14 +3,17 @@
 One step = one esp_eval_walkers call over one batch of walker positions (all
 of the path: spatial ordering and staging, the potential kernel over every
 distribution and point charge, the partial-sum reduction, the per-walker
-energy reduction).
+energy reduction).  One eval = one distribution (or point charge) x one
+position; distributions are counted as the library builds them (after its
+screening and merges), in both arms.
 
-Workload (default): the realistic environment, 2,000 atoms on a jittered
-2.8 bohr lattice outside the 6 bohr QM sphere with cc-pVDZ-shaped primitives
-and a local PSD density (~1.1e6 Hermite distributions after screening at
-1e-12) plus 2,000 nuclei, evaluated at 4,096 walkers x 32 electrons = 131,072
-positions per GPU per step.  One eval = one distribution (or point charge) x
-one position.
+Workload (default `--config large`): the largest configuration, 20,000 atoms on
+a jittered 2.8 bohr lattice (28^3 sites) outside the 6 bohr QM sphere with
+cc-pVDZ-shaped primitives and a local PSD density (~2e7 Hermite
+distributions after screening at 1e-12) plus 20,000 nuclei, evaluated at
+16,384 walkers x 64 electrons = 1,048,576 positions per GPU per step.
+`--config realistic` is the 2,000-atom, 131,072-position configuration, which
+the default run also measures as a secondary leg.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -19,13 +22,13 @@ environment (weak scaling, no collective on the data path); rank 0 prints one
 JSON line.  `--impl reference` times the FP64 CPU oracle on this host's cores
 on a bounded sample of the same workload.
 
-Besides the step, the line carries (rank 0): the FP64 rate on 256 walkers,
-the accuracy of both precisions against the oracle on sampled positions, the
-oracle's own rate (cpu_baseline), the batched leg (64 uneven systems in one
-persistent graph-replayed batch vs separate calls), the few-positions-per-call
-leg (the paper's 268,782 cells, one and 16 positions per call), and the
-surrogate leg (training time, evaluation with fallback vs the exact sum,
-network-only time and errors).
+Besides the step, the line carries (rank 0): the measured pipe peaks, the
+census-based roofline of the FP32C kernel, the FP64 path on 16 whole walkers
+with its own roofline, the accuracy of both precisions (against the oracle,
+or for the large workload against the oracle-checked FP64 path), the oracle's
+own rate (cpu_baseline), the realistic-configuration leg, the batched leg (64
+uneven systems in one persistent graph-replayed batch vs separate calls), the
+few-positions-per-call leg (the paper's 268,782 cells) and the surrogate leg.
 """
 from __future__ import annotations
 
@@ -47,20 +50,75 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gaussian pair×point potential evals/s at ≤1e-5 Ha: FP64 vs FP32 vs surrogate"
 
-# FP32 operations per evaluation by total angular momentum L (offset 3,
-# |r|^2 3, scaled offset 3, T 1-3, Boys 2+2L, Hermite recursion and
-# contraction, accumulate 1).  MUFU work (one rsqrt) is not counted.
-OPS_PER_EVAL = {0: 10, 1: 26, 2: 52, 3: 95, 4: 170}
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+# Algorithmic operation counts per term (one distribution x one position),
+# written out for the McMurchie-Davidson evaluation of one term in plain
+# arithmetic: no compensation (hi/lo words, Newton step, TwoSum), no loads.
+# A multiply, add or fused multiply-add counts 1; the reciprocal square root
+# (MUFU) counts 0 on the FP32 path and 1 on the FP64 path; erfc counts 1.
+#   offset P - C                        3
+#   L = 0: |d|^2 3, T = p |d|^2 1       4      (FP64: p = sqrt(p)^2, +1)
+#   L > 0: x = sqrt(p) d 3, T = |x|^2 3  6
+#   (FP32 asymptotic regime = multipole form on the unscaled offset: |d|^2 3 only)
+#   Hermite recursion R(L), incl. the (-2)^n scaling of each level:
+#                                        0, 4, 17, 46, 100 for L = 0..4
+#   contraction sum G_tuv S_tuv          n_L = 1, 4, 10, 20, 35
+#   accumulate                           1
+# Boys F_0..F_L, by regime of T:
+#   asymptotic (FP32: T >= 30, far/multipole form; FP64: T >= 45):
+#       L = 0: 0 (FP32) / 1 (FP64: sqrt(pi)/2 * rsqrt);  L > 0: 1 + 2L (FP32) / 2 + 2L (FP64)
+#       (h = 1/(2T), F_n = F_{n-1} (2n-1) h)
+#   table (FP32: T < 30, 6 Taylor terms; FP64: T < 45, 9 terms):
+#       row index and remainder 2; F_L by Horner 2 (K-1) + 1;
+#       L > 0: exp(-T) by Horner 2 (K-1) + 1, 2T 1, downward recursion 2L
+#   short-range remainder (monopole moved to a point charge): + 2 (erfc term)
+HERMITE_REC = (0, 4, 17, 46, 100)
+N_HERMITE = (1, 4, 10, 20, 35)
+
+
+def term_ops(L: int, regime: str, fp64: bool, short: bool = False) -> int:
+    """Operations of one term of total angular momentum L in the given Boys
+    regime ("asym" or "table") on the FP32 (fp64=False) or FP64 path."""
+    base = 3 + (4 + (1 if fp64 else 0) if L == 0 else 6) + HERMITE_REC[L] + N_HERMITE[L] + 1
+    if regime == "asym":
+        if not fp64:
+            base -= 1 if L == 0 else 3  # multipole form: |d|^2 only, no T, no scaled offset
+        boys = (1 if fp64 else 0) if L == 0 else (2 if fp64 else 1) + 2 * L
+    else:
+        K = 9 if fp64 else 6
+        boys = 2 + 2 * (K - 1) + 1
+        if L > 0:
+            boys += 2 * (K - 1) + 1 + 1 + 2 * L
+    return base + boys + (2 if short and regime == "table" else 0)
+
+
+POINT_OPS_F64 = 8  # 3 sub, |d|^2 3, Z * rsqrt 1 (+ rsqrt 1 on the FP64 pipe), accumulate
+
+
+def census_ops(census: dict, n_positions: int, fp64: bool):
+    """(algorithmic ops of the distributions, ops of the point charges, terms)
+    of one launch over n_positions, from a work census of a position sample
+    (esp_work_census): FP32 takes the table below T = 30, FP64 below T = 45."""
+    scale = n_positions / census["positions"]
+    ops = 0.0
+    terms = 0
+    for s in (0, 1):
+        for L in range(5):
+            lt30, mid, ge45 = (census["T_lt_30"][s][L], census["T_30_45"][s][L], census["T_ge_45"][s][L])
+            terms += lt30 + mid + ge45
+            if fp64:
+                ops += (lt30 + mid) * term_ops(L, "table", True, s == 1) + ge45 * term_ops(L, "asym", True, s == 1)
+            else:
+                ops += lt30 * term_ops(L, "table", False, s == 1) + (mid + ge45) * term_ops(L, "asym", False, s == 1)
+    return ops * scale, census["point_terms"] * scale * POINT_OPS_F64, terms * scale
 
 
 def keep_heap():
     try:
         import ctypes
         libc = ctypes.CDLL("libc.so.6")
-        libc.mallopt(-4, 0)
-        libc.mallopt(-1, 1 << 30)
+        libc.mallopt(-4, 0)        # M_MMAP_MAX: serve large blocks from the heap
+        libc.mallopt(-1, 1 << 30)  # M_TRIM_THRESHOLD: do not trim the heap
+        libc.mallopt(-8, 1)        # M_ARENA_MAX: the generator's threads share one (non-trimming) arena
     except (OSError, AttributeError):
         pass
 
@@ -139,34 +197,42 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, n_pos: int):
+def profiled_traffic(kernel: str, n_pos: int, kind: str):
     """DRAM bytes of one launch, from the committed ncu counters of a launch of
-    this size; None if the size differs or the kernel source changed since
-    the capture."""
+    this workload and size; None if none was taken or the kernel source changed
+    since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
-    e = t.get(kernel)
+    e = t.get("%s/%s" % (kernel, kind))
     if not e or e.get("source_hash") != kernel_source_hash() or e.get("positions") != n_pos:
         return None
     return e["dram_bytes"]
 
 
-def workload_label(wl, large: bool = False, reduced: bool = False) -> str:
+WORKLOADS = {
+    # the largest configuration: 20,000 atoms on a 28^3 lattice, 16,384 walkers x 64 electrons
+    "large": dict(config=5, n_atoms=20000, n_walkers=16384, n_elec=64, n_side=28),
+    # the realistic configuration: 2,000 atoms, 4,096 walkers x 32 electrons
+    "realistic": dict(config=2, n_atoms=2000, n_walkers=4096, n_elec=32, n_side=None),
+}
+
+
+def workload_label(wl, kind: str, reduced: bool = False) -> str:
     """The workload as both arms of the benchmark name it."""
     return (("REDUCED (profiling) " if reduced else "") +
-            ("large: 20,000 atoms" if large else "realistic: 2,000 atoms") +
-            ", cc-pVDZ-shaped primitives, local PSD density, %d positions (%d walkers x %d electrons) per GPU"
-            % (wl.n_walkers * wl.n_elec, wl.n_walkers, wl.n_elec))
+            "%s: %s atoms, cc-pVDZ-shaped primitives, local PSD density, %d positions (%d walkers x %d electrons) "
+            "per GPU" % (kind, format(WORKLOADS[kind]["n_atoms"], ","), wl.n_walkers * wl.n_elec, wl.n_walkers,
+                         wl.n_elec))
 
 
-def replica_positions(rank: int, n: int) -> np.ndarray:
+def replica_positions(rank: int, n: int, kind: str = "large") -> np.ndarray:
     """The walkers of rank > 0 under torchrun: the same law, a seed of the rank's
     own (rank 0 keeps the workload's positions)."""
     from workloads import seed_for_config, qm_positions
-    return qm_positions(np.random.default_rng(seed_for_config(2) * 1000 + rank), n)
+    return qm_positions(np.random.default_rng(seed_for_config(WORKLOADS[kind]["config"]) * 1000 + rank), n)
 
 
 def max_over_ranks(ms: float, world: int, device: str) -> float:
@@ -179,27 +245,41 @@ def max_over_ranks(ms: float, world: int, device: str) -> float:
     return float(t.item())
 
 
-def build_workload(rank: int, walkers: int = 4096, large: bool = False):
-    from workloads import realistic_environment, seed_for_config, qm_positions
-    if large:
-        # 20,000 atoms on a 28^3 lattice (same per-atom law), 16,384 walkers x 64 electrons
-        wl = realistic_environment(seed=seed_for_config(5), n_atoms=20000, n_walkers=16384, n_elec=64, n_side=28)
-    else:
-        wl = realistic_environment(seed=seed_for_config(2))
+def build_workload(kind: str, rank: int = 0, walkers: int = 0):
+    from workloads import realistic_environment, seed_for_config
+    w = WORKLOADS[kind]
+    wl = realistic_environment(seed=seed_for_config(w["config"]), n_atoms=w["n_atoms"], n_walkers=w["n_walkers"],
+                               n_elec=w["n_elec"], n_side=w["n_side"])
     if rank > 0:
-        wl.positions = replica_positions(rank, wl.n_walkers * wl.n_elec)
-    if walkers != wl.n_walkers:
+        wl.positions = replica_positions(rank, wl.n_walkers * wl.n_elec, kind)
+    if walkers and walkers != wl.n_walkers:
         wl.positions = wl.positions[: walkers * wl.n_elec].copy()
         wl.n_walkers = walkers
     return wl
 
 
-def sample_indices(wl, n_walkers=2, n_outer=32):
-    """Whole walkers (the first and the last) and the positions closest to the environment."""
+def workload_config(wl, kind: str, units: dict, world: int, reduced: bool = False) -> dict:
+    """config of the JSON line, identical in both arms: the workload and the
+    library's unit count (Hermite distributions + point charges per position)."""
+    n = wl.n_walkers * wl.n_elec
+    return {"workload": workload_label(wl, kind, reduced), "distributions": int(units["n_distributions"]),
+            "point_charges": int(units["n_point_charges"]), "positions_per_step": n,
+            "evals_per_step_per_gpu": int((units["n_distributions"] + units["n_point_charges"]) * n),
+            "l2": "inputs larger than L2 (records %s) and L2 flushed between timed steps (512 MB write)"
+                  % ("~1.6 GB" if kind == "large" else "~90 MB"),
+            "parallelism": "replicas (own walkers per GPU, same environment)" if world > 1 else "single GPU"}
+
+
+def sample_indices(wl, n_walkers: int, n_outer: int, n_random: int, seed: int = 17):
+    """Whole walkers (spread over the batch), the positions closest to the
+    environment, and seeded random positions: (walker ids, position indices)."""
     r = np.linalg.norm(wl.positions, axis=1)
     outer = np.argsort(-r)[:n_outer]
-    ws = [0, wl.n_walkers - 1][:n_walkers]
-    return ws, np.concatenate([np.arange(w * wl.n_elec, (w + 1) * wl.n_elec) for w in ws] + [outer])
+    ws = np.unique(np.linspace(0, wl.n_walkers - 1, n_walkers).round().astype(int))
+    walk = np.concatenate([np.arange(w * wl.n_elec, (w + 1) * wl.n_elec) for w in ws])
+    rest = np.setdiff1d(np.arange(wl.n_positions), np.concatenate([walk, outer]))
+    rnd = np.random.default_rng(seed).choice(rest, size=min(n_random, rest.size), replace=False)
+    return ws, np.concatenate([walk, outer, np.sort(rnd)])
 
 
 def _gen_batched(n_sys):
@@ -400,15 +480,28 @@ def latency_leg(args, esp, torch, stream):
     return out
 
 
+def host_units(wl):
+    """The library's unit count of the environment (distributions after its
+    screening and merges + point charges), from a host-only build that touches
+    no GPU."""
+    from paper_1011_4687_gb300 import build_lib, esp
+    build_lib.build()
+    with esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, flags=esp.FLAG_HOST_ONLY) as env:
+        return env.info()
+
+
 def run_reference(args):
-    """The oracle as it stands, on this host's cores, bounded sample per step."""
+    """The oracle as it stands, on this host's cores, on a bounded sample of the
+    headline workload per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     oracle.build()
-    wl = build_workload(0)
-    n_units = (wl.meta["n_shell_pairs"] + wl.nuclei_Z.size)
+    wl = build_workload(args.config, 0, args.walkers)
+    units = host_units(wl)
+    cfg = workload_config(wl, args.config, units, args.gpus, args.walkers not in (0, WORKLOADS[args.config]["n_walkers"]))
+    per_pos = units["n_distributions"] + units["n_point_charges"]
     sample = np.arange(args.ref_positions)
     times = []
     for k in range(args.warmup + args.steps):
@@ -418,86 +511,90 @@ def run_reference(args):
         if k >= args.warmup:
             times.append(dt)
     per = statistics.mean(times)
-    val = n_units * sample.size / per
+    val = per_pos * sample.size / per
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_label(wl), "distributions": wl.meta["n_shell_pairs"],
-                       "point_charges": int(wl.nuclei_Z.size), "oracle_positions_per_step": int(sample.size)},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": val, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": "%d positions of the realistic workload per step (all distributions)"
-                                       % sample.size},
+                             "sample": "%d positions of the workload per step x all %d distributions + point "
+                                       "charges (the library's unit count)" % (sample.size, per_pos)},
             "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def main(argv=None):
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-walkers", type=int, default=256, help="walkers in the FP64 rate measurement")
-    ap.add_argument("--ref-positions", type=int, default=32, help="positions per oracle step (reference arm)")
-    ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-systems leg")
-    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
-    ap.add_argument("--no-latency", action="store_true", help="skip the one-position-per-call leg")
-    ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched leg")
-    ap.add_argument("--walkers", type=int, default=4096,
-                    help="walkers of 32 electrons per GPU (the benchmark workload is 4096; fewer only for profiling)")
-    ap.add_argument("--large", action="store_true",
-                    help="the large configuration instead: 20,000 atoms, 16,384 walkers x 64 electrons")
-    args = ap.parse_args(argv)
-    keep_heap()
-    if args.impl == "reference":
-        return run_reference(args)
-
-    # the batched leg's systems come from a spawn-started pool, before any CUDA call
-    batch_wls = None
-    if not args.no_batch and int(os.environ.get("RANK", "0")) == 0:
-        batch_wls = _gen_batched(args.batch_systems)
-
+def timed_device(fn, stream, flush, k):
+    """Mean device time (ms, CUDA events on `stream`) of k calls of fn, L2 flushed before each."""
     import torch
-    import torch.distributed as dist
-    from paper_1011_4687_gb300 import build_lib, esp
+    ts = []
+    for _ in range(k):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        fn()
+        s1.record(stream)
+        s1.synchronize()
+        ts.append(s0.elapsed_time(s1))
+    return statistics.mean(ts)
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        build_lib.build()
-    if world > 1:
-        dist.barrier()
-    esp.load()
 
-    if args.large:
-        args.walkers = 16384
-    wl = build_workload(rank, args.walkers, large=args.large)
-    stream = torch.cuda.current_stream()
-    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
+def accuracy_leg(wl, kind, env, V, E, torch, oracle_mod):
+    """FP32C errors of the timed step's own outputs.  realistic: against the FP64
+    oracle on 1,024 positions (512 closest to the environment, 512 random) and
+    16 whole walkers.  large: against the library's FP64 path (itself checked
+    against the oracle to 1e-10 in the tests) on the same sample shape, and the
+    FP64 path against the oracle on 16 of those positions."""
+    ws, sample = sample_indices(wl, 16, 512, 512)
+    n_walk = ws.size * wl.n_elec
+    Vs = V.cpu().numpy()[sample]
+    Es = E.cpu().numpy()[ws]
+    env.set_precision("fp64")
+    V64 = env.eval(torch.from_numpy(wl.positions[sample]).cuda())
+    torch.cuda.synchronize()
+    V64 = V64.cpu().numpy()
+    env.set_precision("fp32c")
+    sub = sample if kind == "realistic" else sample[n_walk:n_walk + 16]
+    t0 = time.perf_counter()
+    ref = oracle_mod.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions[sub])
+    t_or = time.perf_counter() - t0
+    out = {"sample": "%d whole walkers (%d positions) + 512 outermost + 512 random positions" % (ws.size, n_walk)}
+    if kind == "realistic":
+        Eref = oracle_mod.walker_energies(ref[:n_walk], ws.size, wl.n_elec)
+        out.update({"against": "FP64 oracle",
+                    "fp32c_max_point_err_ha": float(np.abs(Vs - ref).max()),
+                    "fp32c_max_walker_err_ha": float(np.abs(Es - Eref).max()),
+                    "fp64_max_rel_err": float(np.max(np.abs(V64 - ref) / np.maximum(np.abs(ref), 1.0)))})
+    else:
+        E64 = -V64[:n_walk].reshape(ws.size, wl.n_elec).sum(1)
+        k = slice(n_walk, n_walk + 16)
+        out.update({"against": "the library's FP64 path (oracle on 16 of the positions)",
+                    "fp32c_max_point_err_ha": float(np.abs(Vs - V64).max()),
+                    "fp32c_max_walker_err_ha": float(np.abs(Es - E64).max()),
+                    "fp32c_max_point_err_vs_oracle_ha": float(np.abs(Vs[k] - ref).max()),
+                    "fp64_max_rel_err_vs_oracle": float(np.max(np.abs(V64[k] - ref) / np.maximum(np.abs(ref), 1.0)))})
+    return out, sub.size, t_or
+
+
+def fp32c_step_leg(args, wl, kind, env, esp, torch, stream, flush, world, local, peaks):
+    """K timed steps of the whole path (esp_eval_walkers, FP32C) with clocks,
+    kernel times, census-based roofline and the end-to-end rate."""
     info = env.info()
     n_pos = wl.n_positions
-    units_per_pos = info["n_distributions"] + info["n_point_charges"]
-    evals_per_step = units_per_pos * n_pos
+    units = info["n_distributions"] + info["n_point_charges"]
+    evals = units * n_pos
     pos = torch.from_numpy(wl.positions).cuda()
     V = torch.empty(n_pos, dtype=torch.float64, device="cuda")
     E = torch.empty(wl.n_walkers, dtype=torch.float64, device="cuda")
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-
     env.set_timing(True)
     for _ in range(args.warmup):
         env.eval_walkers(pos, wl.n_walkers, wl.n_elec, V_out=V, E_out=E)
     torch.cuda.synchronize()
-
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kern_ms = []
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -509,124 +606,190 @@ def main(argv=None):
             kern_ms.append(env.last_timing()[0])
         torch.cuda.synchronize()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
+    ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
     ms_max = max_over_ranks(ms, world, "cuda")
-    value = evals_per_step * world / (ms_max * 1e-3)
     kern = statistics.mean(kern_ms)
-    clocks = clk.summary()
-
     # end to end through the public API with pinned host buffers
     pin_pos = torch.from_numpy(wl.positions).pin_memory()
-    pin_V = torch.empty(n_pos, dtype=torch.float64).pin_memory()
-    pin_E = torch.empty(wl.n_walkers, dtype=torch.float64).pin_memory()
-    hp, hv, he = pin_pos.numpy(), pin_V.numpy(), pin_E.numpy()
-    env.eval_walkers(hp, wl.n_walkers, wl.n_elec, V_out=hv, E_out=he)
+    hv = torch.empty(n_pos, dtype=torch.float64).pin_memory().numpy()
+    he = torch.empty(wl.n_walkers, dtype=torch.float64).pin_memory().numpy()
+    hp = pin_pos.numpy()
     e2e_t = []
-    for k in range(args.steps):
+    for _ in range(min(args.steps, args.e2e_steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         env.eval_walkers(hp, wl.n_walkers, wl.n_elec, V_out=hv, E_out=he)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_val = evals_per_step * world / statistics.mean(e2e_t)
+    # roofline of the potential kernel: algorithmic FP32 ops from a census of
+    # 512 of the step's positions, against the measured FFMA lane-op rate
+    cs = env.work_census(wl.positions[np.linspace(0, n_pos - 1, 512).astype(int)])
+    ops, pt_ops, terms = census_ops(cs, n_pos, fp64=False)
+    achieved = ops / (kern * 1e-3)
+    peak = peaks["fp32_fma_per_s"]
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s (FP32 lane ops)",
+            "frac": achieved / peak, "traffic": profiled_traffic("potential_f32c_kernel", n_pos, kind),
+            "kernel": "potential_f32c_kernel", "kernel_ms": kern,
+            "algorithmic_ops_per_launch": ops, "ops_per_distribution_term": ops / max(terms, 1.0),
+            "peak_source": "measured FFMA lane-op rate (esp_measure_peaks, %d SMs read from the device) of measured"
+                           % peaks["num_sms"],
+            "census": cs}
+    res = {"value": evals * world / (ms_max * 1e-3), "ms_per_step": ms_max, "kernel_ms": kern,
+           "clocks": clk.summary(), "roofline": roof, "units": units, "evals": evals,
+           "e2e": {"value": evals * world / statistics.mean(e2e_t), "unit": "evals/s",
+                   "h2d_bytes_per_step": int(n_pos * 24), "d2h_bytes_per_step": int(n_pos * 8 + wl.n_walkers * 8),
+                   "steps": len(e2e_t)},
+           "gpu_launches_per_step": 7 if n_pos >= 4096 else 4, "info": info}
+    return res, pos, V, E
 
-    # FP64 rate on a subset of walkers (same environment, same kernels' FP64 variant)
-    nw64 = min(args.fp64_walkers, wl.n_walkers)
-    pos64 = pos[: nw64 * wl.n_elec].contiguous()
+
+def fp64_leg(args, wl, env, torch, stream, flush, peaks):
+    """The FP64 path on 16 whole walkers of the workload (time and roofline
+    against the measured DFMA lane-op rate)."""
+    nw = min(16, wl.n_walkers)
+    n = nw * wl.n_elec
+    pos = torch.from_numpy(wl.positions[:n].copy()).cuda()
+    info = env.info()
+    units = info["n_distributions"] + info["n_point_charges"]
     env.set_precision("fp64")
-    env.eval_walkers(pos64, nw64, wl.n_elec)
+    env.eval_walkers(pos, nw, wl.n_elec)
     torch.cuda.synchronize()
-    f64 = []
-    for _ in range(2):
-        flush.zero_()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        env.eval_walkers(pos64, nw64, wl.n_elec)
-        s1.record(stream)
-        s1.synchronize()
-        f64.append(s0.elapsed_time(s1))
-    fp64_val = units_per_pos * nw64 * wl.n_elec / (statistics.mean(f64) * 1e-3)
-    env.set_precision("fp32c")
 
+    def one():
+        env.eval_walkers(pos, nw, wl.n_elec)
+
+    ms = timed_device(one, stream, flush, 2)
+    kms = env.last_timing()[0]  # potential kernel of the last timed call
+    env.set_precision("fp32c")
+    cs = env.work_census(wl.positions[:min(n, 512)])
+    ops, pt_ops, terms = census_ops(cs, n, fp64=True)
+    achieved = (ops + pt_ops) / (kms * 1e-3)
+    return {"value": units * n / (ms * 1e-3), "unit": "evals/s", "positions_per_step": n,
+            "sample": "%d whole walkers x %d electrons of the workload" % (nw, wl.n_elec), "ms_per_step": ms,
+            "roofline": {"bound": "fp64", "achieved": achieved / 1e12, "peak": peaks["fp64_fma_per_s"] / 1e12,
+                         "unit": "Tops/s (FP64 lane ops)", "frac": achieved / peaks["fp64_fma_per_s"],
+                         "kernel": "potential_f64_kernel", "kernel_ms": kms,
+                         "ops_per_distribution_term": ops / max(terms, 1.0),
+                         "peak_source": "measured DFMA lane-op rate (esp_measure_peaks) of measured"}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large", choices=sorted(WORKLOADS),
+                    help="headline workload (default: the largest configuration)")
+    ap.add_argument("--ref-positions", type=int, default=2, help="positions per oracle step (reference arm)")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end (host buffer) measurement")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the realistic-configuration leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-systems leg")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--no-latency", action="store_true", help="skip the one-position-per-call leg")
+    ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched leg")
+    ap.add_argument("--walkers", type=int, default=0,
+                    help="walkers per GPU of the headline workload (0: the configuration's own; fewer only for "
+                         "profiling, and the line then says REDUCED)")
+    args = ap.parse_args(argv)
+    keep_heap()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    reduced = args.walkers not in (0, WORKLOADS[args.config]["n_walkers"])
+
+    # workloads are generated before any CUDA call (the batched systems in a
+    # spawn-started pool, the others on threads)
+    batch_wls = None
+    if not args.no_batch and rank == 0:
+        batch_wls = _gen_batched(args.batch_systems)
+    wl = build_workload(args.config, rank, args.walkers)
+    wl2 = None
+    if not args.no_secondary and rank == 0 and args.config != "realistic":
+        wl2 = build_workload("realistic")
+
+    import torch
+    import torch.distributed as dist
+    from paper_1011_4687_gb300 import build_lib, esp
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    esp.load()
+    peaks = esp.measure_peaks(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
+    head, pos, V, E = fp32c_step_leg(args, wl, args.config, env, esp, torch, stream, flush, world, local, peaks)
+    f64 = fp64_leg(args, wl, env, torch, stream, flush, peaks)
     if rank != 0:
         env.close()
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    # roofline of the potential kernel (FP32 issue bound)
-    peaks, peak_src = measured_peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6
-    ops_launch = n_pos * sum(OPS_PER_EVAL[L] * info["n_by_L"][L] for L in range(5))
-    achieved = ops_launch / (kern * 1e-3)
-    traffic = profiled_traffic("potential_f32c_kernel", n_pos)
-
-    out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+    out = {"metric": METRIC, "value": head["value"], "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": workload_label(wl, args.large, not args.large and args.walkers != 4096),
-                      "distributions": info["n_distributions"], "point_charges": info["n_point_charges"],
-                      "precision": "FP32C (FP32 pair sum, compensated; nuclei and near blocks FP64)",
-                      "distributions_by_L": info["n_by_L"], "evals_per_step_per_gpu": evals_per_step,
-                      "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas" if world > 1 else "single"},
-           # per step: spatial order (3 launches, FP32C calls of >= 4,096 positions), stage, potential,
-           # reduce, walker energies
-           "gpu_launches": (7 if n_pos >= 4096 else 4) * args.steps,
-           "clocks": clocks,
-           "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                        "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": traffic,
-                        "kernel": "potential_f32c_kernel", "kernel_ms": kern,
-                        "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_src)},
-           "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": int(n_pos * 24),
-                   "d2h_bytes_per_step": int(n_pos * 8 + wl.n_walkers * 8)},
-           "fp64": {"value": fp64_val, "unit": "evals/s", "positions_per_step": nw64 * wl.n_elec,
-                    "ms_per_step": statistics.mean(f64)}}
-
+           "config": workload_config(wl, args.config, head["info"], world, reduced),
+           "path": {"precision": "FP32C (FP32 pair sum, compensated; nuclei and near blocks FP64)",
+                    "distributions_by_L": head["info"]["n_by_L"],
+                    "step": "esp_eval_walkers: spatial order (3 launches), stage, potential, reduce, walker energies"},
+           "gpu_launches": head["gpu_launches_per_step"] * args.steps,
+           "clocks": head["clocks"], "roofline": head["roofline"], "e2e": head["e2e"], "fp64": f64,
+           "peaks_measured": peaks}
+    oracle_mod = None
     if not args.no_oracle:
         import oracle
         oracle.build()
-        nws, nout = (1, 16) if args.large else (2, 32)
-        ws, sample = sample_indices(wl, nws, nout)
-        t0 = time.perf_counter()
-        ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions[sample])
-        t_or = time.perf_counter() - t0
-        Vs = V.cpu().numpy()[sample]
-        Es = E.cpu().numpy()[ws]
-        Eref = oracle.walker_energies(ref[: nws * wl.n_elec], nws, wl.n_elec)
-        env.set_precision("fp64")
-        V64 = env.eval(torch.from_numpy(wl.positions[sample]).cuda())
-        torch.cuda.synchronize()
-        V64 = V64.cpu().numpy()
-        out["accuracy"] = {"sample": "%d whole walker(s) + %d outermost positions" % (nws, nout),
-                           "fp32c_max_point_err_ha": float(np.abs(Vs - ref).max()),
-                           "fp32c_max_walker_err_ha": float(np.abs(Es - Eref).max()),
-                           "fp64_max_rel_err": float(np.max(np.abs(V64 - ref) / np.maximum(np.abs(ref), 1.0)))}
-        out["cpu_baseline"] = {"value": units_per_pos * sample.size / t_or, "unit": "evals/s",
-                               "cores": oracle.max_threads(), "kind": "oracle",
-                               "sample": "%d positions x all %d distributions + point charges"
-                                         % (sample.size, units_per_pos)}
+        oracle_mod = oracle
+        acc, n_or, t_or = accuracy_leg(wl, args.config, env, V, E, torch, oracle)
+        out["accuracy"] = acc
+        per_pos = head["units"]
+        out["cpu_baseline"] = {"value": per_pos * n_or / t_or, "unit": "evals/s", "cores": oracle.max_threads(),
+                               "kind": "oracle",
+                               "sample": "%d positions of the workload x all %d distributions + point charges"
+                                         % (n_or, per_pos)}
+    del pos, V, E
     env.close()
+
+    if wl2 is not None:
+        env2 = esp.Environment(wl2.nuclei_xyz, wl2.nuclei_Z, wl2.pairs, precision="fp32c", stream=stream.cuda_stream)
+        a2 = argparse.Namespace(**vars(args))
+        h2, pos2, V2, E2 = fp32c_step_leg(a2, wl2, "realistic", env2, esp, torch, stream, flush, 1, local, peaks)
+        leg = {"workload": workload_label(wl2, "realistic"), "value": h2["value"], "unit": "evals/s",
+               "ms_per_step": h2["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
+               "clocks": h2["clocks"], "roofline": h2["roofline"], "e2e": h2["e2e"],
+               "fp64": fp64_leg(args, wl2, env2, torch, stream, flush, peaks)}
+        if oracle_mod is not None:
+            leg["accuracy"], _, _ = accuracy_leg(wl2, "realistic", env2, V2, E2, torch, oracle_mod)
+        out["realistic"] = leg
+        del pos2, V2, E2
+        env2.close()
     if batch_wls is not None:
-        out["batch"] = batch_leg(args, esp, torch, stream, flush, batch_wls,
-                                 None if args.no_oracle else __import__("oracle"))
+        out["batch"] = batch_leg(args, esp, torch, stream, flush, batch_wls, oracle_mod)
         del batch_wls
     if not args.no_latency:
         out["few_positions_per_call"] = latency_leg(args, esp, torch, stream)
     if not args.no_surrogate:
-        out["surrogate"] = surrogate_leg(args, esp, torch, stream, flush,
-                                         None if args.no_oracle else __import__("oracle"))
-    if not args.no_oracle:
-        # the paper's framing, one CPU core (8 of the sampled positions); last,
-        # because it leaves the oracle's OpenMP pool at one thread
-        import oracle
+        out["surrogate"] = surrogate_leg(args, esp, torch, stream, flush, oracle_mod)
+    if oracle_mod is not None:
+        # the paper's framing, one CPU core (one position of the headline
+        # workload); last, because it leaves the oracle's OpenMP pool at one thread
         t1 = time.perf_counter()
-        oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions[sample[:8]], threads=1)
-        out["cpu_baseline"]["single_core_value"] = units_per_pos * 8 / (time.perf_counter() - t1)
+        oracle_mod.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions[:1], threads=1)
+        out["cpu_baseline"]["single_core_value"] = head["units"] * 1 / (time.perf_counter() - t1)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

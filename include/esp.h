@@ -382,6 +382,48 @@ esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_o
 esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int64_t n,
                                double *V_out);
 
+/* Largest sample accepted by esp_work_census. */
+#define ESP_CENSUS_MAX_POSITIONS 4000
+
+/* Work census of an evaluation at the host positions [n][3] (n <=
+ * ESP_CENSUS_MAX_POSITIONS): every (distribution, position) term of the
+ * context's environment, counted by the regime of its Boys argument
+ * T = p |P - C|^2 (Sec. II.B, Eq. ElectrostaticField generalised to Hermite
+ * Gaussian distributions; the regime decides which form of F_n(T) a term
+ * needs and so its operation count).  counts (int64, 31 entries):
+ *   counts[(L + 5 s) * 3 + b]  L = 0..4 total angular momentum, s = 1 for
+ *                              distributions whose monopole sits in a point
+ *                              charge (short-range remainder), b = 0: T < 30,
+ *                              1: 30 <= T < 45, 2: T >= 45;
+ *   counts[30]                 point-charge terms.
+ * Synchronous; allocates and frees a small device buffer.  Errors:
+ * ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_CUDA, ESP_ERR_OOM. */
+esp_status esp_work_census(esp_ctx *ctx, const double *positions, int64_t n, int64_t *counts);
+
+/* ------------------------------------------------------------------------
+ * Measured pipe peaks of the GPU: the denominators of the potential kernels'
+ * rooflines.  The paper estimates its hardware's peaks from unit counts and
+ * clocks (Sec. IV, Table performances) and sets its kernel against them; this
+ * call measures them instead.  Each rate is instructions per second summed
+ * over all lanes ("lane ops"; an FMA counts once), from kernels of independent
+ * dependency chains on every SM (8 CTAs of 256 threads per SM), timed with
+ * CUDA events on the default stream after one warm-up launch.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double fp32_fma_per_s;    /* FFMA lane ops / s */
+    double fp64_fma_per_s;    /* DFMA lane ops / s */
+    double mufu_rsqrt_per_s;  /* MUFU reciprocal square root, lane ops / s */
+    double mufu_ex2_per_s;    /* MUFU base-2 exponential, lane ops / s */
+    double fp32_ms, fp64_ms, rsqrt_ms, ex2_ms; /* duration of one timed launch */
+    int32_t num_sms;          /* cudaDevAttrMultiProcessorCount of the device */
+    int32_t clock_khz;        /* cudaDevAttrClockRate (the rated, not the live clock) */
+} esp_peaks;
+
+/* Measure the peaks on `device` (< 0: the current device).  Synchronous; takes
+ * tens of milliseconds; allocates (and frees) a few KB of device memory.
+ * Errors: ESP_ERR_INVALID (out NULL), ESP_ERR_CUDA, ESP_ERR_OOM. */
+esp_status esp_measure_peaks(int32_t device, esp_peaks *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@ from . import build_lib
 
 ESP_OK, ESP_ERR_INVALID, ESP_ERR_OOM, ESP_ERR_CUDA, ESP_ERR_TIMEOUT, ESP_ERR_STATE, ESP_ERR_UNSUPPORTED = range(7)
 FP64, FP32C = 0, 1
+FLAG_HOST_ONLY = 1  # esp_options.flags: build on the host only, touch no GPU
 PRECISIONS = {"fp64": FP64, "fp32c": FP32C}
 
 GAUSS_PAIR_DTYPE = np.dtype([("A", "<f8", (3,)), ("alpha", "<f8"), ("lmn_a", "<i4", (3,)), ("pad_a", "<i4"),
@@ -85,6 +86,16 @@ class SurrogateStats(ctypes.Structure):
                 ("trusted_fraction", ctypes.c_double), ("n_params", ctypes.c_int64), ("n_baseline", ctypes.c_int64),
                 ("valid_rms_err", ctypes.c_double), ("baseline_max_err", ctypes.c_double),
                 ("baseline_rms_err", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double),
+                ("mufu_rsqrt_per_s", ctypes.c_double), ("mufu_ex2_per_s", ctypes.c_double),
+                ("fp32_ms", ctypes.c_double), ("fp64_ms", ctypes.c_double), ("rsqrt_ms", ctypes.c_double),
+                ("ex2_ms", ctypes.c_double), ("num_sms", ctypes.c_int32), ("clock_khz", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -174,6 +185,10 @@ def load(build_if_missing: bool = False):
     lib.esp_surrogate_debug_net.restype = ctypes.c_int
     lib.esp_surrogate_destroy.argtypes = [P]
     lib.esp_surrogate_destroy.restype = None
+    lib.esp_work_census.argtypes = [P, P, i64, P]
+    lib.esp_work_census.restype = ctypes.c_int
+    lib.esp_measure_peaks.argtypes = [i32, ctypes.POINTER(Peaks)]
+    lib.esp_measure_peaks.restype = ctypes.c_int
     lib.esp_set_timing.argtypes = [P, i32]
     lib.esp_set_timing.restype = ctypes.c_int
     lib.esp_last_timing.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -231,7 +246,7 @@ class Environment:
 
     def __init__(self, nuclei_xyz, nuclei_Z, pairs, precision="fp32c", screen_tol=1e-12,
                  qm_center=(0.0, 0.0, 0.0), stream=None, device=-1, tile_size=0, threads_per_block=0,
-                 positions_per_thread=0, pair_splits=0, near_radius=-1.0):
+                 positions_per_thread=0, pair_splits=0, near_radius=-1.0, flags=0):
         lib = load()
         opt = default_options()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -244,6 +259,7 @@ class Environment:
         opt.positions_per_thread = int(positions_per_thread)
         opt.pair_splits = int(pair_splits)
         opt.near_radius = float(near_radius)
+        opt.flags = int(flags)
         ch = pack_charges(nuclei_xyz, nuclei_Z)
         pr = pack_pairs(pairs)
         w = np.ascontiguousarray(pairs.w, np.float64)
@@ -333,12 +349,29 @@ class Environment:
         _check(load().esp_eval_walkers(self._ctx, pp, int(n_walkers), int(n_elec), pv, pe))
         return V_out, E_out
 
+    def work_census(self, positions: np.ndarray) -> dict:
+        """Terms per (L, short-range, Boys band) at host positions (esp_work_census):
+        {"far30": [5], "mid": [5], "far45": [5] ... } keyed as below, counts over all positions."""
+        pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+        c = np.zeros(31, np.int64)
+        _check(load().esp_work_census(self._ctx, pos.ctypes.data, pos.shape[0], c.ctypes.data))
+        t = c[:30].reshape(2, 5, 3)  # [short][L][band]
+        return {"positions": int(pos.shape[0]), "T_lt_30": t[:, :, 0].tolist(), "T_30_45": t[:, :, 1].tolist(),
+                "T_ge_45": t[:, :, 2].tolist(), "point_terms": int(c[30])}
+
     def debug_host_eval(self, positions: np.ndarray) -> np.ndarray:
         """Test hook: evaluate the built tiles on the host in FP64 (never used by eval)."""
         pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
         V = np.zeros(pos.shape[0])
         _check(load().esp_debug_host_eval(self._ctx, pos.ctypes.data, pos.shape[0], V.ctypes.data))
         return V
+
+
+def measure_peaks(device: int = -1) -> dict:
+    """Measured FFMA / DFMA / MUFU lane-op rates of the device (esp_measure_peaks)."""
+    p = Peaks()
+    _check(load().esp_measure_peaks(int(device), ctypes.byref(p)))
+    return p.as_dict()
 
 
 def debug_boys(precision, nmax: int, T: float) -> np.ndarray:

@@ -18,6 +18,7 @@ def _keep_heap():
         libc = ctypes.CDLL("libc.so.6")
         libc.mallopt(-4, 0)            # M_MMAP_MAX: serve large blocks from the heap
         libc.mallopt(-1, 1 << 30)      # M_TRIM_THRESHOLD: do not trim the heap
+        libc.mallopt(-8, 1)            # M_ARENA_MAX: the generator's threads share that one arena
     except (OSError, AttributeError):
         pass
 
