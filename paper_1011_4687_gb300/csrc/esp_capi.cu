@@ -32,69 +32,70 @@ namespace {
 
 } // namespace
 
-int esp::choose_splits(const esp_ctx *c, int n, int prec)
+int esp::choose_splits(const esp_ctx *c, const TileView &v, int n, int prec)
 {
     if (c->opt.pair_splits > 0)
-        return std::max(1, std::min(c->opt.pair_splits, std::max(c->n_tiles, 1)));
+        return std::max(1, std::min(c->opt.pair_splits, std::max(v.n_tiles, 1)));
     int per_cta = c->threads[prec] * c->ppt[prec];
     int blocks = (n + per_cta - 1) / per_cta;
     // many short CTAs: the round-robin deal of tiles balances, and the last
     // wave leaves little idle time (measured best at ~50 CTAs per SM)
     int target = 48 * c->num_sms;
     int s = (target + blocks - 1) / blocks;
-    s = std::min(s, std::max(c->n_tiles, 1));
+    s = std::min(s, std::max(v.n_tiles, 1));
     s = std::min(s, 64);
     return std::max(s, 1);
 }
 
-int esp::plan_splits(const esp_ctx *c, int n, int prec, int max_splits, EvalArgs &a)
+int esp::plan_splits(const esp_ctx *c, const TileView &v, int n, int prec, int max_splits, EvalArgs &a)
 {
-    const int total = std::max(1, std::min(choose_splits(c, n, prec), max_splits));
-    a.n_tiles = c->n_tiles;
+    const int total = std::max(1, std::min(choose_splits(c, v, n, prec), max_splits));
+    a.n_tiles = v.n_tiles;
+    a.tiles = v.tiles;
     a.n_splits = total;
     single_group(a);
-    if (prec == 0 || c->opt.pair_splits > 0 || c->n_groups <= 1 || c->n_groups > total)
+    if (prec == 0 || c->opt.pair_splits > 0 || v.n_groups <= 1 || v.n_groups > total)
         return total;
     double work = 0.0;
-    for (int g = 0; g < c->n_groups; ++g)
-        work += c->grp_work[g];
+    for (int g = 0; g < v.n_groups; ++g)
+        work += v.grp_work[g];
     int S[kMaxTileGroups], sum = 0;
-    for (int g = 0; g < c->n_groups; ++g) {
-        const int tiles = c->grp_tile[g + 1] - c->grp_tile[g];
-        const int want = int(std::lround(total * c->grp_work[g] / std::max(work, 1e-300)));
+    for (int g = 0; g < v.n_groups; ++g) {
+        const int tiles = v.grp_tile[g + 1] - v.grp_tile[g];
+        const int want = int(std::lround(total * v.grp_work[g] / std::max(work, 1e-300)));
         S[g] = std::max(1, std::min(want, tiles));
         sum += S[g];
     }
     while (sum > total) { // give back from the group with the most splits
         int big = 0;
-        for (int g = 1; g < c->n_groups; ++g)
+        for (int g = 1; g < v.n_groups; ++g)
             if (S[g] > S[big])
                 big = g;
         --S[big];
         --sum;
     }
-    a.n_groups = c->n_groups;
+    a.n_groups = v.n_groups;
     a.grp_split[0] = 0;
-    for (int g = 0; g < c->n_groups; ++g) {
-        a.grp_tile[g] = c->grp_tile[g];
+    for (int g = 0; g < v.n_groups; ++g) {
+        a.grp_tile[g] = v.grp_tile[g];
         a.grp_split[g + 1] = a.grp_split[g] + S[g];
     }
-    a.grp_tile[c->n_groups] = c->grp_tile[c->n_groups];
+    a.grp_tile[v.n_groups] = v.grp_tile[v.n_groups];
     a.n_splits = sum;
     return sum;
 }
 
-void esp::set_tile_groups(esp_ctx *c)
+void esp::set_tile_groups(const std::vector<TileMeta> &T, TileView &v)
 {
     // FP32 operations per evaluation by L (the kernel's algorithmic count) and
     // an FP64 point charge, for the split of the work between groups
     static const double kCost[kMaxL + 1] = {10.0, 26.0, 52.0, 95.0, 170.0};
     const double kPointCost = 12.0;
-    const auto &T = c->env.tiles;
-    c->n_groups = 1;
-    c->grp_tile[0] = 0;
-    c->grp_tile[1] = int(T.size());
-    c->grp_work[0] = 0.0;
+    v.n_tiles = int(T.size());
+    v.n_groups = 1;
+    v.grp_tile[0] = 0;
+    v.grp_tile[1] = int(T.size());
+    v.grp_work[0] = 0.0;
     int n = 0, prev = -1;
     int bounds[kMaxTileGroups + 1];
     double work[kMaxTileGroups] = {0.0};
@@ -113,11 +114,11 @@ void esp::set_tile_groups(esp_ctx *c)
     if (n == 0)
         return;
     bounds[n] = int(T.size());
-    c->n_groups = n;
+    v.n_groups = n;
     for (int g = 0; g <= n; ++g)
-        c->grp_tile[g] = bounds[g];
+        v.grp_tile[g] = bounds[g];
     for (int g = 0; g < n; ++g)
-        c->grp_work[g] = work[g];
+        v.grp_work[g] = work[g];
 }
 
 namespace {
@@ -131,10 +132,7 @@ esp_status ensure_scratch(esp_ctx *c, int64_t n, int splits, bool host_io, int64
         return cuda_fail(e, "allocating staged positions");
     if ((e = c->partial.ensure(size_t(n) * splits * sizeof(double))) != cudaSuccess)
         return cuda_fail(e, "allocating partial sums");
-    if ((e = c->vout.ensure(size_t(n) * sizeof(double))) != cudaSuccess)
-        return cuda_fail(e, "allocating potentials");
-    if (n_walkers > 0 && (e = c->eout.ensure(size_t(n_walkers) * sizeof(double))) != cudaSuccess)
-        return cuda_fail(e, "allocating walker energies");
+    (void)n_walkers;
     return ESP_OK;
 }
 
@@ -155,7 +153,80 @@ Staged staged_view(esp_ctx *c, int64_t n)
     return st;
 }
 
-// The evaluation pipeline shared by esp_eval and esp_eval_walkers.
+// The device part of an evaluation over the view's tiles, enqueued on the
+// context's stream: spatial order (FP32C, >= kSortMinPositions positions),
+// staging, potential kernel (or the few-position path), fixed-order reduction
+// into dV, and the walker energies into dE when dE is set.  timing: record
+// ev[1] / ev[2] around the potential kernel.
+esp_status pipeline(esp_ctx *c, const TileView &v, int prec, const double *d_pos, int64_t n, double *dV,
+                    int64_t n_walkers, int64_t n_elec, double *dE, bool timing)
+{
+    // few positions: entries spread over threads instead of positions
+    const bool small_n = n <= kSmallN && v.n_tiles > 0;
+    EvalArgs a;
+    const int splits = small_n ? small_n_splits(v.n_tiles, c->num_sms) : plan_splits(c, v, int(n), prec, 1 << 20, a);
+    esp_status st = ensure_scratch(c, n, splits, false, n_walkers);
+    if (st != ESP_OK)
+        return st;
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    // FP32C with many positions: stage them in spatial order (the kernel's
+    // warp-uniform far/near votes then see compact groups of positions)
+    const bool sorted = !small_n && prec == 1 && n >= kSortMinPositions;
+    if (sorted && (e = c->sortbuf.ensure(sort_scratch_ints(int(n)) * sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "allocating the position order");
+    Staged stg = staged_view(c, n);
+    int *slot_of = nullptr, *perm = nullptr;
+    if (sorted && (e = launch_sort(d_pos, int(n), c->opt.qm_center, static_cast<int *>(c->sortbuf.p), &slot_of, &perm,
+                                   s)) != cudaSuccess)
+        return cuda_fail(e, "ordering positions");
+    // (the few-position kernel reads and recentres the positions itself)
+    if (!small_n && (e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s, slot_of)) !=
+                        cudaSuccess)
+        return cuda_fail(e, "staging positions");
+    a.n_pos = int(n);
+    a.tile_size = c->env.tile_size;
+    a.pos = stg;
+    a.tiles = v.tiles;
+    a.rec32 = static_cast<const float *>(c->rec32.p);
+    a.rec64 = static_cast<const double *>(c->rec64.p);
+    a.boys32 = static_cast<const float *>(c->boys32.p);
+    a.boys64 = static_cast<const double *>(c->boys64.p);
+    a.partial = static_cast<double *>(c->partial.p);
+    a.near_r = float(c->opt.near_radius < 0.0 ? kDefaultNearRadius : c->opt.near_radius);
+    if (timing && (e = cudaEventRecord(c->ev[1], s)) != cudaSuccess)
+        return cuda_fail(e, "recording a timing event");
+    if (v.n_tiles == 0) {
+        if ((e = cudaMemsetAsync(a.partial, 0, size_t(n) * splits * sizeof(double), s)) != cudaSuccess)
+            return cuda_fail(e, "clearing partial sums");
+    } else if (small_n) {
+        SmallArgs sa;
+        sa.n_pos = int(n);
+        sa.n_tiles = v.n_tiles;
+        sa.pos_in = d_pos;
+        sa.cx = c->opt.qm_center[0];
+        sa.cy = c->opt.qm_center[1];
+        sa.cz = c->opt.qm_center[2];
+        sa.tiles = v.tiles;
+        sa.rec64 = a.rec64;
+        sa.boys64 = a.boys64;
+        sa.partial = a.partial;
+        if ((e = launch_small_n(sa, splits, dV, s)) != cudaSuccess)
+            return cuda_fail(e, "launching the few-position kernels");
+    } else if ((e = launch_potential(prec, a, c->threads[prec], c->ppt[prec], s)) != cudaSuccess) {
+        return cuda_fail(e, "launching the potential kernel");
+    }
+    if (timing && (e = cudaEventRecord(c->ev[2], s)) != cudaSuccess)
+        return cuda_fail(e, "recording a timing event");
+    if ((!small_n || v.n_tiles == 0) && (e = launch_reduce(a.partial, splits, int(n), dV, s, perm)) != cudaSuccess)
+        return cuda_fail(e, "launching the partial-sum reduction");
+    if (dE && (e = launch_walkers(dV, int(n_walkers), int(n_elec), dE, s)) != cudaSuccess)
+        return cuda_fail(e, "launching the walker-energy reduction");
+    return ESP_OK;
+}
+
+// The evaluation shared by esp_eval and esp_eval_walkers: argument checks,
+// host <-> device copies around the pipeline over every tile.
 esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_out, int64_t n_walkers,
                     int64_t n_elec, double *E_out)
 {
@@ -179,20 +250,16 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
                                      "device %d", c->device);
     const bool host_io = sp == Space::Host;
     const int prec = c->opt.precision == ESP_FP64 ? 0 : 1;
-    // few positions: entries spread over threads instead of positions
-    const bool small_n = n <= kSmallN && c->n_tiles > 0;
-    EvalArgs a;
-    const int splits = small_n ? small_n_splits(c->n_tiles, c->num_sms) : plan_splits(c, int(n), prec, 1 << 20, a);
-    esp_status st = ensure_scratch(c, n, splits, host_io, n_walkers);
-    if (st != ESP_OK)
-        return st;
     cudaStream_t s = c->stream;
     cudaError_t e;
-    // FP32C with many positions: stage them in spatial order (the kernel's
-    // warp-uniform far/near votes then see compact groups of positions)
-    const bool sorted = !small_n && prec == 1 && n >= kSortMinPositions;
-    if (sorted && (e = c->sortbuf.ensure(sort_scratch_ints(int(n)) * sizeof(int))) != cudaSuccess)
-        return cuda_fail(e, "allocating the position order");
+    if (host_io) {
+        if ((e = c->in.ensure(size_t(n) * 3 * sizeof(double))) != cudaSuccess ||
+            (e = c->vout.ensure(size_t(n) * sizeof(double))) != cudaSuccess ||
+            (n_walkers > 0 && (e = c->eout.ensure(size_t(n_walkers) * sizeof(double))) != cudaSuccess))
+            return cuda_fail(e, "allocating host-call staging");
+    } else if (!V_out && (e = c->vout.ensure(size_t(n) * sizeof(double))) != cudaSuccess) {
+        return cuda_fail(e, "allocating potentials");
+    }
     c->timed_valid = false;
     if (c->timing && (e = cudaEventRecord(c->ev[0], s)) != cudaSuccess)
         return cuda_fail(e, "recording a timing event");
@@ -203,58 +270,11 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
             return cuda_fail(e, "copying positions to the device");
         d_pos = static_cast<const double *>(c->in.p);
     }
-    Staged stg = staged_view(c, n);
-    int *slot_of = nullptr, *perm = nullptr;
-    if (sorted && (e = launch_sort(d_pos, int(n), c->opt.qm_center, static_cast<int *>(c->sortbuf.p), &slot_of, &perm,
-                                   s)) != cudaSuccess)
-        return cuda_fail(e, "ordering positions");
-    // (the few-position kernel reads and recentres the positions itself)
-    if (!small_n && (e = launch_stage(d_pos, int(n), c->opt.qm_center, c->env.coord_quantum, stg, s, slot_of)) !=
-                        cudaSuccess)
-        return cuda_fail(e, "staging positions");
-    a.n_pos = int(n);
-    a.tile_size = c->env.tile_size;
-    a.pos = stg;
-    a.tiles = static_cast<const TileMeta *>(c->tiles.p);
-    a.rec32 = static_cast<const float *>(c->rec32.p);
-    a.rec64 = static_cast<const double *>(c->rec64.p);
-    a.boys32 = static_cast<const float *>(c->boys32.p);
-    a.boys64 = static_cast<const double *>(c->boys64.p);
-    a.partial = static_cast<double *>(c->partial.p);
-    a.near_r = float(c->opt.near_radius < 0.0 ? kDefaultNearRadius : c->opt.near_radius);
-    if (c->timing && (e = cudaEventRecord(c->ev[1], s)) != cudaSuccess)
-        return cuda_fail(e, "recording a timing event");
     double *dV = (!host_io && V_out) ? V_out : static_cast<double *>(c->vout.p);
-    if (c->n_tiles == 0) {
-        if ((e = cudaMemsetAsync(a.partial, 0, size_t(n) * splits * sizeof(double), s)) != cudaSuccess)
-            return cuda_fail(e, "clearing partial sums");
-    } else if (small_n) {
-        SmallArgs sa;
-        sa.n_pos = int(n);
-        sa.n_tiles = c->n_tiles;
-        sa.pos_in = d_pos;
-        sa.cx = c->opt.qm_center[0];
-        sa.cy = c->opt.qm_center[1];
-        sa.cz = c->opt.qm_center[2];
-        sa.tiles = a.tiles;
-        sa.rec64 = a.rec64;
-        sa.boys64 = a.boys64;
-        sa.partial = a.partial;
-        if ((e = launch_small_n(sa, splits, dV, s)) != cudaSuccess)
-            return cuda_fail(e, "launching the few-position kernels");
-    } else if ((e = launch_potential(prec, a, c->threads[prec], c->ppt[prec], s)) != cudaSuccess) {
-        return cuda_fail(e, "launching the potential kernel");
-    }
-    if (c->timing && (e = cudaEventRecord(c->ev[2], s)) != cudaSuccess)
-        return cuda_fail(e, "recording a timing event");
-    if (!small_n && (e = launch_reduce(a.partial, splits, int(n), dV, s, perm)) != cudaSuccess)
-        return cuda_fail(e, "launching the partial-sum reduction");
-    double *dE = nullptr;
-    if (E_out) {
-        dE = host_io ? static_cast<double *>(c->eout.p) : E_out;
-        if ((e = launch_walkers(dV, int(n_walkers), int(n_elec), dE, s)) != cudaSuccess)
-            return cuda_fail(e, "launching the walker-energy reduction");
-    }
+    double *dE = E_out ? (host_io ? static_cast<double *>(c->eout.p) : E_out) : nullptr;
+    esp_status st = pipeline(c, c->full, prec, d_pos, n, dV, n_walkers, n_elec, dE, c->timing);
+    if (st != ESP_OK)
+        return st;
     if (c->timing) {
         if ((e = cudaEventRecord(c->ev[3], s)) != cudaSuccess)
             return cuda_fail(e, "recording a timing event");
@@ -273,6 +293,22 @@ esp_status run_eval(esp_ctx *c, const double *positions, int64_t n, double *V_ou
     }
     return ESP_OK;
 }
+
+} // namespace
+
+esp_status esp::eval_view(esp_ctx *c, const TileView &v, int prec, const double *d_pos, int64_t n, double *d_V)
+{
+    if (n < 0 || n > (int64_t(1) << 30))
+        return fail(ESP_ERR_INVALID, "position count %lld out of range", (long long)n);
+    if (n == 0)
+        return ESP_OK;
+    DeviceGuard dg(c->device);
+    if (!dg.ok)
+        return fail(ESP_ERR_CUDA, "cannot select device %d", c->device);
+    return pipeline(c, v, prec, d_pos, n, d_V, 0, 0, nullptr, false);
+}
+
+namespace {
 
 template <typename T>
 cudaError_t upload(DevBuf &b, const std::vector<T> &v, int64_t &bytes)
@@ -444,7 +480,7 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const 
         return fail(st, "%s", err.c_str());
     }
     c->n_tiles = int(c->env.tiles.size());
-    set_tile_groups(c);
+    set_tile_groups(c->env.tiles, c->full);
     if (opt.flags & ESP_FLAG_HOST_ONLY) {
         c->device = -1;
         *out = c;
@@ -490,6 +526,7 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const 
         return cuda_fail(e, "uploading the environment");
     }
     c->device_bytes = bytes;
+    c->full.tiles = static_cast<const TileMeta *>(c->tiles.p);
     // keep a host copy of the records only while it is small (test hook use)
     if (c->env.rec64.size() * sizeof(double) > (size_t(256) << 20)) {
         c->host_copy = false;
@@ -755,7 +792,7 @@ extern "C" esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, in
         return st;
     const int prec = ctx->opt.precision == ESP_FP64 ? 0 : 1;
     EvalArgs a;
-    const int splits = plan_splits(ctx, int(n), prec, kNoallocMaxSplits, a);
+    const int splits = plan_splits(ctx, ctx->full, int(n), prec, kNoallocMaxSplits, a);
     char *b = static_cast<char *>(base);
     Staged stg;
     stg.x64 = reinterpret_cast<double *>(b);

@@ -108,6 +108,23 @@ inline Space classify(const void *p, int device)
     return Space::Host;
 }
 
+// A set of a context's tiles evaluated together: the whole environment, or a
+// subset (the surrogate's near-field tiles).  `tiles` is a device array of
+// TileMeta (records stay in the context's rec32 / rec64); the FP32C splits
+// are dealt per class group (point charges, L = 0..4; empty groups left out),
+// in proportion to each group's estimated FP32 work.
+struct TileView {
+    const TileMeta *tiles = nullptr;
+    int n_tiles = 0;
+    int n_groups = 1;
+    int grp_tile[kMaxTileGroups + 1] = {0, 0};
+    double grp_work[kMaxTileGroups] = {0.0};
+};
+
+// Tile groups of a host tile list (in device order); with fewer than one
+// group per class, or tiles not grouped by class, the plain deal.
+void set_tile_groups(const std::vector<TileMeta> &T, TileView &v);
+
 } // namespace esp
 
 struct esp_ctx {
@@ -122,11 +139,7 @@ struct esp_ctx {
     std::atomic<int> busy{0};
     int64_t device_bytes = 0;
     int n_tiles = 0;
-    // FP32C tile groups (points, L = 0..4; empty groups left out): tile ranges
-    // and estimated FP32 work, set at creation
-    int n_groups = 1;
-    int grp_tile[esp::kMaxTileGroups + 1] = {0, 0};
-    double grp_work[esp::kMaxTileGroups] = {0.0};
+    esp::TileView full;      // every tile of the environment, set at creation
     int threads[2] = {128, 128};  // per precision (0 = FP64, 1 = FP32C)
     int ppt[2] = {2, 4};
     bool timing = false;
@@ -138,11 +151,15 @@ struct esp_ctx {
 namespace esp {
 inline bool valid_ctx(const esp_ctx *c) { return c && c->magic == 0x45535021u; }
 // per-split count for n positions in precision prec (0 FP64, 1 FP32C)
-int choose_splits(const esp_ctx *c, int n, int prec);
-// Fills the deal of a's tiles (n_splits and the tile groups) for n positions,
-// with at most max_splits partial sums; returns n_splits.  FP32C deals each
-// tile group to its own splits, in proportion to the group's work.
-int plan_splits(const esp_ctx *c, int n, int prec, int max_splits, EvalArgs &a);
-// Tile groups of the built environment (at creation).
-void set_tile_groups(esp_ctx *c);
+int choose_splits(const esp_ctx *c, const TileView &v, int n, int prec);
+// Fills the deal of the view's tiles (n_splits and the tile groups) for n
+// positions, with at most max_splits partial sums; returns n_splits.  FP32C
+// deals each tile group to its own splits, in proportion to the group's work.
+int plan_splits(const esp_ctx *c, const TileView &v, int n, int prec, int max_splits, EvalArgs &a);
+// Potentials of the view's tiles at n device positions into device V (the
+// main pipeline of esp_eval: spatial order for FP32C calls of >= 4,096
+// positions, staging, potential kernel, fixed-order reduction), enqueued on
+// the context's stream with the context's scratch.  prec: 0 FP64, 1 FP32C.
+// The caller holds the context (no other call may run on it meanwhile).
+esp_status eval_view(esp_ctx *c, const TileView &v, int prec, const double *d_pos, int64_t n, double *d_V);
 } // namespace esp

@@ -100,10 +100,10 @@ def test_noalloc_sizes_vs_oracle_and_no_memory_growth():
         stream.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0
         assert torch.cuda.memory_allocated() == alloc0
-        pick = np.concatenate([np.arange(8), np.arange(n_max - 8, n_max), np.arange(1000, n_max, 4099)])
+        pick = np.concatenate([np.arange(16), np.arange(n_max - 8, n_max), np.arange(1000, n_max, 4099)])
         ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos_np[pick])
         assert np.abs(V.cpu().numpy()[pick] - ref).max() <= FP32_POINT
-        for n in (1, 5, 16):
+        for n in (1, 5, 16):  # pick[:16] are positions 0..15
             Vn = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
             _noalloc(lib, env, pos[:n].contiguous(), Vn)
             stream.synchronize()
