@@ -253,24 +253,32 @@ esp_status esp_batch_last_ms(esp_batch *b, double *ms);
 void esp_batch_destroy(esp_batch *b);
 
 /* ------------------------------------------------------------------------
- * Learned surrogate of V over the QM region (the QM sphere about qm_center).
- * V_sur = FP64 Legendre-product baseline + BF16 tensor-core MLP on the
- * residual (64 Fourier features, 4 x 256 SiLU, scalar out), trained by the
- * library's own forward/backward kernels and Adam on exact FP64 labels.  The
- * exact kernel stays the fallback: positions in voxels whose validation error
+ * Learned surrogate of V over the QM region (the QM sphere of radius
+ * qm_radius about the context's qm_center).  The environment is split once:
+ * near tiles (any part closer to the centre than far_radius, or Gaussians
+ * reaching into the sphere) are summed exactly on every call by the FP32C
+ * kernel; the far tiles' potential, harmonic inside the sphere, is replaced by
+ * its FP64 interior solid-harmonic expansion of degree `degree` (coefficients
+ * projected from the exact far field on the sphere) plus a BF16 tensor-core
+ * MLP on the remaining residual (64 Fourier features, 4 x 256 SiLU, scalar
+ * out), trained by the library's own forward/backward kernels and Adam on
+ * labels of the exact kernel over the far tiles.  The exact sum over all
+ * tiles stays the fallback: positions in voxels whose validation error
  * exceeded tol/2, near point charges, or picked by the online probe are
- * evaluated exactly, and a failed probe withdraws its voxel for later calls.
- * The paper has no surrogate; the exact sum it accelerates decides its error.
+ * evaluated exactly; a probe that misses tol withdraws its voxel, and the
+ * call's other positions in that voxel are evaluated exactly before it
+ * returns.  The paper has no surrogate; the exact sum it accelerates decides
+ * the surrogate's error.
  * ------------------------------------------------------------------------ */
 typedef struct esp_surrogate esp_surrogate;
 
 typedef struct {
     int32_t size;              /* sizeof(esp_surrogate_cfg), set by esp_surrogate_default_cfg */
-    int32_t n_train;           /* training positions (2^22) */
-    int32_t n_valid;           /* validation positions for the trust map (2^18) */
-    int32_t epochs;            /* passes over the training set (6) */
+    int32_t n_train;           /* training positions (2^19) */
+    int32_t n_valid;           /* validation positions for the trust map (2^17) */
+    int32_t epochs;            /* passes over the training set (8) */
     int32_t batch;             /* mini-batch (8192) */
-    int32_t degree;            /* Legendre degree of the baseline (10; <= 16) */
+    int32_t degree;            /* degree L of the far field's interior expansion (16; <= 40) */
     double qm_radius;          /* radius of the QM sphere, bohr (6) */
     double position_sd;        /* sd of the walker law for half the samples (2) */
     double fourier_sigma;      /* sd of the Fourier frequencies, per unit radius (1) */
@@ -279,23 +287,27 @@ typedef struct {
     double voxel;              /* trust-map voxel edge, bohr (0.25) */
     double nucleus_exclusion;  /* positions this close to a point charge fall back, bohr (0.5) */
     int32_t probe_stride;      /* every probe_stride-th position is also evaluated exactly (64; 0 off) */
-    int32_t pad;
+    int32_t label_precision;   /* exact kernel of the training and validation labels (ESP_FP32C; or ESP_FP64) */
     uint64_t seed;             /* positions, frequencies and initial weights (1011) */
+    double far_radius;         /* tiles wholly beyond this distance from the centre form the far field,
+                                  bohr (12; >= qm_radius) */
 } esp_surrogate_cfg;
 
 typedef struct {
     int64_t n_fallback;        /* positions of the last call evaluated exactly */
     int64_t n_probe_fail;      /* probes that missed tol (last call; total in esp_surrogate_info) */
-    double surrogate_ms;       /* baseline + network time of the last call */
+    double surrogate_ms;       /* near sum + expansion + network time of the last call */
     double total_ms;           /* the whole last call, fallback included */
     double train_loss;         /* final training loss (normalised residual) */
-    double valid_max_err;      /* largest validation error of baseline + network, Ha */
+    double valid_max_err;      /* largest validation error of expansion + network on the far field, Ha */
     double trusted_fraction;   /* share of visited voxels trusted */
     int64_t n_params;          /* network parameters */
-    int64_t n_baseline;        /* baseline coefficients */
-    double valid_rms_err;      /* rms validation error of baseline + network, Ha */
-    double baseline_max_err;   /* the same two errors of the baseline alone (without the network) */
+    int64_t n_baseline;        /* expansion coefficients, (degree + 1)^2 */
+    double valid_rms_err;      /* rms validation error of expansion + network, Ha */
+    double baseline_max_err;   /* the same two errors of the expansion alone (without the network) */
     double baseline_rms_err;
+    int64_t n_near_entries;    /* distributions + point charges summed exactly on every call */
+    int64_t n_far_entries;     /* distributions + point charges replaced by expansion + network */
 } esp_surrogate_stats;
 
 void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg);
@@ -329,6 +341,11 @@ esp_status esp_surrogate_load(esp_ctx *ctx, const char *path, esp_surrogate **ou
 esp_status esp_surrogate_debug_step(esp_surrogate *s, const double *positions, const float *targets, int32_t n,
                                     float *params_out, float *grad_out, float *y_out);
 esp_status esp_surrogate_features(const esp_surrogate *s, float *freq_out, double *centre_inv_r_out);
+/* Test hook: add dc to the constant coefficient c_00 of the far-field
+ * expansion (dc = 0: no change), then copy the first max_coef coefficients to
+ * coef_out (esp_harmonics order).  Adding an offset plants a known error in
+ * every surrogate value, which the probe must catch. */
+esp_status esp_surrogate_debug_expansion(esp_surrogate *s, double dc, double *coef_out, int32_t max_coef);
 /* Test hook: the network outputs y [n] (FP32 normalised residual, before the
  * baseline and scale are applied) of the fused tensor-core inference kernel
  * (tcgen05) at host positions [n][3], n <= 65536.  ESP_ERR_TIMEOUT if one of
@@ -372,6 +389,14 @@ int32_t esp_abi_version(void);
  * host (nmax <= ESP_MAX_L).  Lets CPU tests check the tables and the Taylor
  * and asymptotic branches without a GPU. */
 esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_out);
+
+/* Test hook, not part of the evaluation path: the real regular solid
+ * harmonics S_k(u), k < (L + 1)^2 (L <= 40), that the surrogate's far-field
+ * expansion uses, evaluated on the host by the device code's recursion, at
+ * the point u[3]; out gets (L + 1)^2 values in the order (l, 0), (l, 1, cos),
+ * (l, 1, sin), ... for l = 0..L.  They are |u|^l times the real spherical
+ * harmonics normalised to 4 pi over the unit sphere. */
+esp_status esp_debug_solid_harmonics(int32_t L, const double *u, double *out);
 
 /* Test hook, not part of the evaluation path: evaluate a built context's
  * tiles on the host with the kernels' own per-tile code, in the context's

@@ -19,6 +19,7 @@
 #include "../../include/esp.h"
 #include "esp_ctx.h"
 #include "esp_eval_core.h"
+#include "esp_harmonics.h"
 
 using namespace esp;
 
@@ -709,6 +710,20 @@ esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_o
         return ESP_OK;
     }
     return fail(ESP_ERR_INVALID, "unknown precision");
+}
+
+esp_status esp_debug_solid_harmonics(int32_t L, const double *u, double *out)
+{
+    if (L < 0 || L > kMaxExpDegree || !u || !out)
+        return fail(ESP_ERR_INVALID, "bad solid-harmonic arguments");
+    static HarmonicConsts h;
+    static bool ready = false;
+    if (!ready) {
+        harmonic_consts(h);
+        ready = true;
+    }
+    solid_harmonics(u[0], u[1], u[2], L, h.a, h.b, h.sec, h.sub, [&](int k, double v) { out[k] = v; });
+    return ESP_OK;
 }
 
 esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int64_t n, double *V_out)

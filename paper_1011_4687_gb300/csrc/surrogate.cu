@@ -1,24 +1,37 @@
 // Learned surrogate of the environment potential over the QM region.
 //
-// V_sur(r) = B(u) + s * f_theta(u),  u = (r - centre) / R
-//   B       : FP64 least-squares fit of V by products of Legendre polynomials
-//             P_a(ux) P_b(uy) P_c(uz), a + b + c <= degree;
-//   f_theta : MLP on Fourier features (see surrogate_kernels.cu), trained on
-//             the normalised residual (V - B) / s with the library's own BF16
-//             tensor-core forward/backward kernels and Adam; inference runs
-//             the whole network in one tcgen05 kernel (surrogate_tc.cu).
+//   V_sur(r) = V_near(r) + sum_lm c_lm S_lm(u) + s f_theta(u),  u = (r - centre) / R
+//
+// V_near : the exact sum (FP32C potential kernel) over the near tiles: every
+//          tile whose bounding sphere comes closer to the centre than
+//          `far_radius`, or whose Gaussians reach into the QM sphere
+//          (p_min (d - R)^2 < 30); near nuclei are therefore always summed
+//          exactly;
+// c_lm   : FP64 interior expansion of the far tiles' potential, which is
+//          harmonic inside the QM sphere (esp_harmonics.h): each coefficient is
+//          the projection of the far field on Y_lm over the sphere |u| = 1,
+//          computed by Gauss-Legendre x trapezoid quadrature of the far field
+//          evaluated there by the exact FP64 kernel (exact up to aliasing from
+//          degrees >= L + 25, which fall off as (R / far_radius)^l);
+// f_theta: MLP on Fourier features (surrogate_kernels.cu) trained on the
+//          normalised residual (V_far - expansion) / s of the far field with
+//          the library's own BF16 tensor-core forward/backward kernels and
+//          Adam, labels from the exact kernel over the far tiles; inference
+//          runs the whole network in one tcgen05 kernel (surrogate_tc.cu).
 // Training positions follow the walker law (half) and fill the sphere
-// uniformly (half); labels come from the FP64 exact kernel.  A voxel map,
-// built from validation against the exact kernel, marks where the surrogate
-// meets the tolerance; positions elsewhere, near point charges, or picked by
-// the online probe (every probe_stride-th position) are evaluated exactly,
-// and a probe that misses the tolerance withdraws its voxel for later calls.
+// uniformly (half).  A voxel map, built from validation against the exact
+// far-tile sum, marks where expansion + network meet the tolerance; positions
+// elsewhere, near point charges, or picked by the online probe (every
+// probe_stride-th position) are evaluated exactly over all tiles.  A probe
+// that misses the tolerance withdraws its voxel, and the positions of the same
+// call in withdrawn voxels are evaluated exactly before the call returns.
 #include <cmath>
 #include <cstdio>
 #include <random>
 #include <vector>
 
 #include "esp_ctx.h"
+#include "esp_harmonics.h"
 #include "surrogate_kernels.h"
 
 using namespace esp;
@@ -62,21 +75,26 @@ struct esp_surrogate {
     double centre[3] = {0, 0, 0};
     double inv_r = 1.0 / 6.0;
     double scale = 1.0;                 // s: residual normalisation
-    int degree = 0, ncoef = 0;
-    std::vector<double> coef;           // baseline coefficients
-    std::vector<int> powers;            // [ncoef][3]
+    int degree = 0, ncoef = 0;          // expansion degree L, (L + 1)^2 coefficients
+    std::vector<double> coef;           // c_lm (esp_harmonics.h order)
     std::vector<float> freq;            // [kFreq][3]
     std::vector<float> params;          // FP32 master copy (host mirror after training)
     std::vector<unsigned char> trust;   // [dim^3]
     int dim = 0;
     double train_loss = 0.0, valid_max_err = 0.0, trusted_fraction = 0.0;
-    double valid_rms_err = 0.0, base_max_err = 0.0, base_rms_err = 0.0; // network vs baseline alone
+    double valid_rms_err = 0.0, base_max_err = 0.0, base_rms_err = 0.0; // with the network / expansion alone
+    int64_t n_near_entries = 0, n_far_entries = 0;
     int probe_offset = 0;
+    // near / far split of the context's tiles
+    std::vector<TileMeta> near_tiles, far_tiles;
+    TileView near_view, far_view;
+    DevBuf d_near_tiles, d_far_tiles;
     // device state
-    DevBuf d_params, d_params_bf, d_grad, d_m, d_v, d_coef, d_powers, d_freq, d_trust;
+    DevBuf d_params, d_params_bf, d_grad, d_m, d_v, d_coef, d_freq, d_trust;
     DevBuf d_X, d_Z, d_H, d_dZ, d_y, d_dy, d_part, d_t, d_loss;   // per-chunk activations
     DevBuf d_flag, d_pre, d_tot, d_count, d_cpos, d_cidx, d_cV, d_nfail;
     DevBuf d_wpk, d_tcerr, d_ynet;      // packed weights, kernel status, fused-inference outputs
+    bool packed = false;                // d_wpk holds the current BF16 parameters
     int ynet_cap = 0;
     int chunk_cap = 0, fb_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
@@ -247,81 +265,6 @@ void sample_positions(std::mt19937_64 &rng, int n, const double *c, double R, do
     }
 }
 
-void legendre(double u, int D, double *P)
-{
-    P[0] = 1.0;
-    if (D >= 1)
-        P[1] = u;
-    for (int l = 1; l < D; ++l)
-        P[l + 1] = ((2 * l + 1) * u * P[l] - l * P[l - 1]) / (l + 1);
-}
-
-// least-squares coefficients of the Legendre-product basis (normal equations,
-// Cholesky, FP64) on m sample points
-bool fit_baseline(esp_surrogate *s, const std::vector<double> &pos, const std::vector<double> &V, int m)
-{
-    const int D = s->degree;
-    s->powers.clear();
-    for (int a = 0; a <= D; ++a)
-        for (int b = 0; a + b <= D; ++b)
-            for (int c = 0; a + b + c <= D; ++c) {
-                s->powers.push_back(a);
-                s->powers.push_back(b);
-                s->powers.push_back(c);
-            }
-    const int nc = int(s->powers.size() / 3);
-    s->ncoef = nc;
-    std::vector<double> A(size_t(nc) * nc, 0.0), rhs(nc, 0.0), row(nc);
-    double P[3][kMaxDegree + 1];
-    for (int i = 0; i < m; ++i) {
-        for (int d = 0; d < 3; ++d)
-            legendre((pos[size_t(i) * 3 + d] - s->centre[d]) * s->inv_r, D, P[d]);
-        for (int k = 0; k < nc; ++k)
-            row[size_t(k)] = P[0][s->powers[3 * k]] * P[1][s->powers[3 * k + 1]] * P[2][s->powers[3 * k + 2]];
-        for (int k = 0; k < nc; ++k) {
-            rhs[size_t(k)] += row[size_t(k)] * V[size_t(i)];
-            for (int j = 0; j <= k; ++j)
-                A[size_t(k) * nc + j] += row[size_t(k)] * row[size_t(j)];
-        }
-    }
-    double tr = 0.0;
-    for (int k = 0; k < nc; ++k)
-        tr += A[size_t(k) * nc + k];
-    for (int k = 0; k < nc; ++k)
-        A[size_t(k) * nc + k] += 1e-13 * tr / nc;
-    // Cholesky A = L L^T (lower triangle in place)
-    for (int j = 0; j < nc; ++j) {
-        double d = A[size_t(j) * nc + j];
-        for (int k = 0; k < j; ++k)
-            d -= A[size_t(j) * nc + k] * A[size_t(j) * nc + k];
-        if (!(d > 0.0))
-            return false;
-        d = std::sqrt(d);
-        A[size_t(j) * nc + j] = d;
-        for (int i = j + 1; i < nc; ++i) {
-            double v = A[size_t(i) * nc + j];
-            for (int k = 0; k < j; ++k)
-                v -= A[size_t(i) * nc + k] * A[size_t(j) * nc + k];
-            A[size_t(i) * nc + j] = v / d;
-        }
-    }
-    std::vector<double> y(nc);
-    for (int i = 0; i < nc; ++i) {
-        double v = rhs[size_t(i)];
-        for (int k = 0; k < i; ++k)
-            v -= A[size_t(i) * nc + k] * y[size_t(k)];
-        y[size_t(i)] = v / A[size_t(i) * nc + i];
-    }
-    s->coef.assign(size_t(nc), 0.0);
-    for (int i = nc - 1; i >= 0; --i) {
-        double v = y[size_t(i)];
-        for (int k = i + 1; k < nc; ++k)
-            v -= A[size_t(k) * nc + i] * s->coef[size_t(k)];
-        s->coef[size_t(i)] = v / A[size_t(i) * nc + i];
-    }
-    return true;
-}
-
 template <typename T>
 cudaError_t upload_vec(DevBuf &b, const std::vector<T> &v)
 {
@@ -347,9 +290,147 @@ TcLayout tc_layout()
     return t;
 }
 
+
+// Near / far split of the context's tiles.  A tile is far when its bounding
+// sphere lies beyond far_radius from the centre and (distributions) every
+// Gaussian of it is negligible inside the QM sphere: p_min (d - R)^2 >= 30,
+// d the distance from the centre to the sphere's nearest point, the FP32
+// kernel's own threshold for the asymptotic (multipole) form.
+void split_tiles(esp_surrogate *s)
+{
+    const double R = 1.0 / s->inv_r, Rs = s->cfg.far_radius;
+    s->near_tiles.clear();
+    s->far_tiles.clear();
+    s->n_near_entries = s->n_far_entries = 0;
+    for (const TileMeta &m : s->ctx->env.tiles) {
+        const double d = std::sqrt(double(m.cx) * m.cx + double(m.cy) * m.cy + double(m.cz) * m.cz) - double(m.rad);
+        bool far = d >= Rs;
+        if (far && m.cls != kClassPoint)
+            far = double(m.pmin) * (d - R) * (d - R) >= 30.0;
+        (far ? s->far_tiles : s->near_tiles).push_back(m);
+        (far ? s->n_far_entries : s->n_near_entries) += m.n;
+    }
+    set_tile_groups(s->near_tiles, s->near_view);
+    set_tile_groups(s->far_tiles, s->far_view);
+}
+
+esp_status upload_split(esp_surrogate *s)
+{
+    cudaError_t e;
+    if ((e = upload_vec(s->d_near_tiles, s->near_tiles)) != cudaSuccess ||
+        (e = upload_vec(s->d_far_tiles, s->far_tiles)) != cudaSuccess)
+        return cuda_fail(e, "uploading the near/far tile split");
+    s->near_view.tiles = static_cast<const TileMeta *>(s->d_near_tiles.p);
+    s->far_view.tiles = static_cast<const TileMeta *>(s->d_far_tiles.p);
+    return ESP_OK;
+}
+
+// Quadrature nodes on the unit sphere for the projection: Gauss-Legendre in
+// cos(theta) (nt nodes) x nf equally spaced phi; weights sum to 4 pi.
+void sphere_quadrature(int nt, int nf, std::vector<double> &dirs, std::vector<double> &w)
+{
+    std::vector<double> x(nt), wx(nt);
+    for (int i = 0; i < nt; ++i) {
+        double z = std::cos(3.14159265358979323846 * (i + 0.75) / (nt + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= nt; ++k) {
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            const double dp = nt * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16)
+                break;
+        }
+        double p0 = 1.0, p1 = 0.0;
+        for (int k = 1; k <= nt; ++k) {
+            const double p2 = p1;
+            p1 = p0;
+            p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+        }
+        const double dp = nt * (z * p0 - p1) / (z * z - 1.0);
+        x[i] = z;
+        wx[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    dirs.clear();
+    w.clear();
+    for (int i = 0; i < nt; ++i) {
+        const double st = std::sqrt(std::max(0.0, 1.0 - x[i] * x[i]));
+        for (int j = 0; j < nf; ++j) {
+            const double ph = 2.0 * 3.14159265358979323846 * j / nf;
+            dirs.push_back(st * std::cos(ph));
+            dirs.push_back(st * std::sin(ph));
+            dirs.push_back(x[i]);
+            w.push_back(wx[i] * 2.0 * 3.14159265358979323846 / nf);
+        }
+    }
+}
+
+const HarmonicConsts &host_harmonics()
+{
+    static HarmonicConsts h;
+    static bool ready = false;
+    if (!ready) {
+        harmonic_consts(h);
+        ready = true;
+    }
+    return h;
+}
+
+// Far-field potentials of the current call into dV (exact kernel over the far
+// tiles; zero when no tile is far).
+esp_status far_exact(esp_surrogate *s, const double *pos, int64_t n, double *dV, int prec)
+{
+    if (s->far_tiles.empty()) {
+        cudaError_t e = cudaMemsetAsync(dV, 0, size_t(n) * sizeof(double), s->ctx->stream);
+        return e == cudaSuccess ? ESP_OK : cuda_fail(e, "clearing far-field values");
+    }
+    return eval_view(s->ctx, s->far_view, prec, pos, n, dV);
+}
+
+// c_lm = (1 / 4 pi) sum_q w_q V_far(centre + R d_q) Y_lm(d_q).
+esp_status project_far_field(esp_surrogate *s)
+{
+    const int L = s->degree;
+    s->ncoef = num_harmonics(L);
+    s->coef.assign(size_t(s->ncoef), 0.0);
+    if (s->far_tiles.empty())
+        return ESP_OK;
+    const int nt = L + 13, nf = 2 * L + 25;
+    std::vector<double> dirs, w;
+    sphere_quadrature(nt, nf, dirs, w);
+    const int nq = int(w.size());
+    const double R = 1.0 / s->inv_r;
+    std::vector<double> qpos(size_t(nq) * 3), Vq(nq);
+    for (int q = 0; q < nq; ++q)
+        for (int d = 0; d < 3; ++d)
+            qpos[size_t(q) * 3 + d] = s->centre[d] + R * dirs[size_t(q) * 3 + d];
+    DevBuf dq, dv;
+    cudaError_t e;
+    if ((e = upload_vec(dq, qpos)) != cudaSuccess || (e = dv.ensure(size_t(nq) * sizeof(double))) != cudaSuccess)
+        return cuda_fail(e, "allocating the projection points");
+    esp_status r = far_exact(s, static_cast<const double *>(dq.p), nq, static_cast<double *>(dv.p), 0);
+    if (r != ESP_OK)
+        return r;
+    if ((e = cudaMemcpyAsync(Vq.data(), dv.p, size_t(nq) * sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s->ctx->stream)) != cudaSuccess)
+        return cuda_fail(e, "far field at the projection points");
+    const HarmonicConsts &h = host_harmonics();
+    for (int q = 0; q < nq; ++q) {
+        const double f = w[size_t(q)] * Vq[size_t(q)] / (4.0 * 3.14159265358979323846);
+        solid_harmonics(dirs[size_t(q) * 3], dirs[size_t(q) * 3 + 1], dirs[size_t(q) * 3 + 2], L, h.a, h.b, h.sec,
+                        h.sub, [&](int k, double v) { s->coef[size_t(k)] += f * v; });
+    }
+    return ESP_OK;
+}
+
 // Network outputs y (FP32, normalised residual) at n device positions, by the
-// fused tensor-core kernel.  The weights are packed from the current BF16
-// parameters on every call (416 KB, one small kernel).
+// fused tensor-core kernel.  The operand copy of the weights is packed once
+// per parameter update (after training or loading), not per call.
 esp_status net_forward(esp_surrogate *s, const double *pos, int n, cudaStream_t st)
 {
     cudaError_t e;
@@ -358,12 +439,15 @@ esp_status net_forward(esp_surrogate *s, const double *pos, int n, cudaStream_t 
             return cuda_fail(e, "allocating surrogate outputs");
         s->ynet_cap = n;
     }
-    if ((e = s->d_wpk.ensure(tc_packed_elems() * 2)) != cudaSuccess || (e = s->d_tcerr.ensure(16)) != cudaSuccess ||
-        (e = cudaMemsetAsync(s->d_tcerr.p, 0, 4, st)) != cudaSuccess)
-        return cuda_fail(e, "allocating packed weights");
     const TcLayout lay = tc_layout();
-    if ((e = tc_pack(static_cast<const __nv_bfloat16 *>(s->d_params_bf.p), lay,
-                     static_cast<__nv_bfloat16 *>(s->d_wpk.p), st)) != cudaSuccess ||
+    if (!s->packed) {
+        if ((e = s->d_wpk.ensure(tc_packed_elems() * 2)) != cudaSuccess || (e = s->d_tcerr.ensure(16)) != cudaSuccess ||
+            (e = tc_pack(static_cast<const __nv_bfloat16 *>(s->d_params_bf.p), lay,
+                         static_cast<__nv_bfloat16 *>(s->d_wpk.p), st)) != cudaSuccess)
+            return cuda_fail(e, "packing the surrogate weights");
+        s->packed = true;
+    }
+    if ((e = cudaMemsetAsync(s->d_tcerr.p, 0, 4, st)) != cudaSuccess ||
         (e = tc_forward(pos, n, static_cast<const float *>(s->d_freq.p), s->centre, s->inv_r,
                         static_cast<const __nv_bfloat16 *>(s->d_wpk.p), static_cast<const float *>(s->d_params.p), lay,
                         static_cast<float *>(s->d_ynet.p), static_cast<int *>(s->d_tcerr.p), st)) != cudaSuccess)
@@ -385,37 +469,40 @@ esp_status net_status(esp_surrogate *s)
     return ESP_OK;
 }
 
-// Surrogate values (baseline + network, no fallback) at n device positions.
+// The far-field approximation (expansion + network) at n device positions:
+// V = (accumulate ? V : 0) + expansion + s y.
+esp_status far_approx(esp_surrogate *s, const double *pos, int n, double *V, bool accumulate, cudaStream_t st)
+{
+    esp_status r = net_forward(s, pos, n, st);
+    if (r != ESP_OK)
+        return r;
+    cudaError_t e = expansion(pos, n, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p), s->degree,
+                              static_cast<const float *>(s->d_ynet.p), s->scale, accumulate, V, st);
+    return e == cudaSuccess ? ESP_OK : cuda_fail(e, "surrogate expansion");
+}
+
+// Surrogate values without fallback: exact near-tile sum + far approximation.
 esp_status predict(esp_surrogate *s, const double *pos, int n, double *V, cudaStream_t st)
 {
     if (n <= 0)
         return ESP_OK;
-    esp_status r = net_forward(s, pos, n, st);
-    if (r != ESP_OK)
+    esp_status r;
+    if (s->near_tiles.empty()) {
+        cudaError_t e = cudaMemsetAsync(V, 0, size_t(n) * sizeof(double), st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "clearing surrogate values");
+    } else if ((r = eval_view(s->ctx, s->near_view, 1, pos, n, V)) != ESP_OK) {
         return r;
-    cudaError_t e = combine(pos, n, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p),
-                            static_cast<const int *>(s->d_powers.p), s->ncoef, s->degree,
-                            static_cast<const float *>(s->d_ynet.p), s->scale, V, st);
-    return e == cudaSuccess ? ESP_OK : cuda_fail(e, "surrogate combine");
-}
-
-esp_status exact_eval(esp_ctx *ctx, const double *pos, int64_t n, double *V, int precision)
-{
-    int32_t old = ctx->opt.precision;
-    esp_status st = esp_set_precision(ctx, precision);
-    if (st != ESP_OK)
-        return st;
-    st = esp_eval(ctx, pos, n, V);
-    esp_status st2 = esp_set_precision(ctx, old);
-    return st != ESP_OK ? st : st2;
+    }
+    return far_approx(s, pos, n, V, true, st);
 }
 
 void release_sur(esp_surrogate *s)
 {
-    DevBuf *bufs[] = {&s->d_params, &s->d_params_bf, &s->d_grad, &s->d_m, &s->d_v, &s->d_coef, &s->d_powers,
-                      &s->d_freq, &s->d_trust, &s->d_X, &s->d_Z, &s->d_H, &s->d_dZ, &s->d_y, &s->d_dy, &s->d_part,
-                      &s->d_t, &s->d_loss, &s->d_flag, &s->d_pre, &s->d_tot, &s->d_count, &s->d_cpos, &s->d_cidx,
-                      &s->d_cV, &s->d_nfail};
+    DevBuf *bufs[] = {&s->d_params, &s->d_params_bf, &s->d_grad, &s->d_m, &s->d_v, &s->d_coef, &s->d_freq,
+                      &s->d_trust, &s->d_X, &s->d_Z, &s->d_H, &s->d_dZ, &s->d_y, &s->d_dy, &s->d_part, &s->d_t,
+                      &s->d_loss, &s->d_flag, &s->d_pre, &s->d_tot, &s->d_count, &s->d_cpos, &s->d_cidx, &s->d_cV,
+                      &s->d_nfail, &s->d_wpk, &s->d_tcerr, &s->d_ynet, &s->d_near_tiles, &s->d_far_tiles};
     for (DevBuf *b : bufs)
         b->release();
     for (cudaEvent_t *e : {&s->ev0, &s->ev1, &s->ev2})
@@ -432,25 +519,51 @@ esp_status init_device(esp_surrogate *s)
     std::vector<__nv_bfloat16> pb(L.total);
     for (size_t i = 0; i < L.total; ++i)
         pb[i] = __float2bfloat16(s->params[i]);
-    if ((e = upload_vec(s->d_params, s->params)) != cudaSuccess || (e = upload_vec(s->d_params_bf, pb)) != cudaSuccess ||
+    if ((e = set_harmonic_consts()) != cudaSuccess || (e = upload_vec(s->d_params, s->params)) != cudaSuccess ||
+        (e = upload_vec(s->d_params_bf, pb)) != cudaSuccess ||
         (e = s->d_grad.ensure(L.total * sizeof(float))) != cudaSuccess ||
         (e = s->d_m.ensure(L.total * sizeof(float))) != cudaSuccess ||
         (e = s->d_v.ensure(L.total * sizeof(float))) != cudaSuccess ||
         (e = cudaMemset(s->d_m.p, 0, L.total * sizeof(float))) != cudaSuccess ||
         (e = cudaMemset(s->d_v.p, 0, L.total * sizeof(float))) != cudaSuccess ||
-        (e = upload_vec(s->d_coef, s->coef)) != cudaSuccess || (e = upload_vec(s->d_powers, s->powers)) != cudaSuccess ||
-        (e = upload_vec(s->d_freq, s->freq)) != cudaSuccess || (e = upload_vec(s->d_trust, s->trust)) != cudaSuccess)
+        (e = upload_vec(s->d_coef, s->coef)) != cudaSuccess || (e = upload_vec(s->d_freq, s->freq)) != cudaSuccess ||
+        (e = upload_vec(s->d_trust, s->trust)) != cudaSuccess)
         return cuda_fail(e, "uploading the surrogate");
+    s->packed = false;
     if (!s->ev0 && ((e = cudaEventCreate(&s->ev0)) != cudaSuccess || (e = cudaEventCreate(&s->ev1)) != cudaSuccess ||
                     (e = cudaEventCreate(&s->ev2)) != cudaSuccess))
         return cuda_fail(e, "creating surrogate events");
+    return upload_split(s);
+}
+
+// Point charges (x, y, z in the caller's frame) within `reach` of the centre,
+// read from the device records of the point tiles that come that close.
+esp_status nearby_point_charges(esp_surrogate *s, double reach, std::vector<double> &pts)
+{
+    const esp_ctx *c = s->ctx;
+    pts.clear();
+    for (const TileMeta &m : c->env.tiles) {
+        if (m.cls != kClassPoint)
+            continue;
+        const double d = std::sqrt(double(m.cx) * m.cx + double(m.cy) * m.cy + double(m.cz) * m.cz) - double(m.rad);
+        if (d > reach)
+            continue;
+        std::vector<double> rec(size_t(m.n) * kPointStride64);
+        cudaError_t e = cudaMemcpy(rec.data(), static_cast<const double *>(c->rec64.p) + m.off64,
+                                   rec.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "reading point charges");
+        for (int j = 0; j < m.n; ++j)
+            for (int d2 = 0; d2 < 3; ++d2)
+                pts.push_back(rec[size_t(j) * kPointStride64 + d2] + c->opt.qm_center[d2]);
+    }
     return ESP_OK;
 }
 
 // Voxel trust map from validation errors: a voxel is trusted when it holds at
 // least one validation point, every such point met tol/2, and no point charge
 // of the environment lies within `exclusion` of the voxel.
-void build_trust(esp_surrogate *s, const std::vector<double> &pos, const std::vector<double> &err)
+esp_status build_trust(esp_surrogate *s, const std::vector<double> &pos, const std::vector<double> &err)
 {
     const double vox = s->cfg.voxel, R = 1.0 / s->inv_r;
     s->dim = int(std::ceil(2.0 * R / vox));
@@ -468,14 +581,10 @@ void build_trust(esp_surrogate *s, const std::vector<double> &pos, const std::ve
     }
     s->trust.assign(vmax.size(), 0);
     const double excl = s->cfg.nucleus_exclusion + 0.87 * vox; // voxel half-diagonal
-    // point charges of the environment (FP64 records of point tiles)
     std::vector<double> pts;
-    const esp_ctx *c = s->ctx;
-    for (const TileMeta &m : c->env.tiles)
-        if (m.cls == kClassPoint && c->host_copy)
-            for (int j = 0; j < m.n; ++j)
-                for (int d = 0; d < 3; ++d)
-                    pts.push_back(c->env.rec64[size_t(m.off64) + 4 * j + d] + c->opt.qm_center[d]);
+    esp_status r = nearby_point_charges(s, h * 1.7321 + excl, pts);
+    if (r != ESP_OK)
+        return r;
     size_t ntrust = 0, nvis = 0;
     for (int ix = 0; ix < dim; ++ix)
         for (int iy = 0; iy < dim; ++iy)
@@ -499,6 +608,17 @@ void build_trust(esp_surrogate *s, const std::vector<double> &pos, const std::ve
                 }
             }
     s->trusted_fraction = nvis ? double(ntrust) / double(nvis) : 0.0;
+    return ESP_OK;
+}
+
+esp_status download(std::vector<double> &out, const DevBuf &b, size_t n, cudaStream_t st)
+{
+    out.resize(n);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(out.data(), b.p, n * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "reading surrogate data");
+    return ESP_OK;
 }
 
 esp_status train(esp_surrogate *s)
@@ -527,53 +647,50 @@ esp_status train(esp_surrogate *s)
         for (int k = 0; k < kHidden; ++k)
             s->params[L.w5 + k] = float(U(rng));
     }
-    // training and validation positions with exact FP64 labels
+    // near / far split and the far field's interior expansion
+    split_tiles(s);
+    s->trust.assign(1, 0);
+    s->ncoef = num_harmonics(s->degree);
+    s->coef.assign(size_t(s->ncoef), 0.0);
+    if ((r = init_device(s)) != ESP_OK || (r = project_far_field(s)) != ESP_OK)
+        return r;
+    if ((e = upload_vec(s->d_coef, s->coef)) != cudaSuccess)
+        return cuda_fail(e, "uploading the expansion");
+    // training and validation positions; labels: the exact far-tile sum
     std::vector<double> tpos, vpos;
     sample_positions(rng, cfg.n_train, s->centre, 1.0 / s->inv_r, cfg.position_sd, tpos);
     sample_positions(rng, cfg.n_valid, s->centre, 1.0 / s->inv_r, cfg.position_sd, vpos);
-    DevBuf d_tpos, d_tV, d_vpos, d_vV, d_vS;
+    DevBuf d_tpos, d_tV, d_tE, d_vpos, d_vV, d_vS;
     if ((e = upload_vec(d_tpos, tpos)) != cudaSuccess || (e = upload_vec(d_vpos, vpos)) != cudaSuccess ||
         (e = d_tV.ensure(size_t(cfg.n_train) * 8)) != cudaSuccess ||
+        (e = d_tE.ensure(size_t(cfg.n_train) * 8)) != cudaSuccess ||
         (e = d_vV.ensure(size_t(cfg.n_valid) * 8)) != cudaSuccess ||
         (e = d_vS.ensure(size_t(cfg.n_valid) * 8)) != cudaSuccess)
         return cuda_fail(e, "allocating surrogate training data");
-    if ((r = exact_eval(ctx, static_cast<const double *>(d_tpos.p), cfg.n_train, static_cast<double *>(d_tV.p),
-                        ESP_FP64)) != ESP_OK ||
-        (r = exact_eval(ctx, static_cast<const double *>(d_vpos.p), cfg.n_valid, static_cast<double *>(d_vV.p),
-                        ESP_FP64)) != ESP_OK)
+    const int lp = cfg.label_precision == ESP_FP64 ? 0 : 1;
+    const double *tp = static_cast<const double *>(d_tpos.p), *vp = static_cast<const double *>(d_vpos.p);
+    if ((r = far_exact(s, tp, cfg.n_train, static_cast<double *>(d_tV.p), lp)) != ESP_OK ||
+        (r = far_exact(s, vp, cfg.n_valid, static_cast<double *>(d_vV.p), lp)) != ESP_OK)
         return r;
-    std::vector<double> tV(cfg.n_train), vV(cfg.n_valid);
-    if ((e = cudaMemcpy(tV.data(), d_tV.p, tV.size() * 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
-        (e = cudaMemcpy(vV.data(), d_vV.p, vV.size() * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_fail(e, "reading training labels");
-    // baseline on a subsample, residual scale on the full set
-    const int mfit = std::min(cfg.n_train, 1 << 16);
-    if (!fit_baseline(s, tpos, tV, mfit))
-        return fail(ESP_ERR_INVALID, "baseline fit is singular (degree too high for the sample)");
-    std::vector<double> base(cfg.n_train);
-    {
-        double P[3][kMaxDegree + 1];
-        double ss = 0.0;
-        for (int i = 0; i < cfg.n_train; ++i) {
-            for (int d = 0; d < 3; ++d)
-                legendre((tpos[size_t(i) * 3 + d] - s->centre[d]) * s->inv_r, s->degree, P[d]);
-            double b = 0.0;
-            for (int k = 0; k < s->ncoef; ++k)
-                b += s->coef[size_t(k)] * P[0][s->powers[3 * k]] * P[1][s->powers[3 * k + 1]] * P[2][s->powers[3 * k + 2]];
-            base[size_t(i)] = tV[size_t(i)] - b;
-            ss += base[size_t(i)] * base[size_t(i)];
-        }
-        s->scale = std::max(std::sqrt(ss / std::max(cfg.n_train, 1)), 1e-300);
+    if ((e = expansion(tp, cfg.n_train, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p), s->degree,
+                       nullptr, 0.0, false, static_cast<double *>(d_tE.p), st)) != cudaSuccess)
+        return cuda_fail(e, "expansion at the training positions");
+    std::vector<double> tV, tE;
+    if ((r = download(tV, d_tV, size_t(cfg.n_train), st)) != ESP_OK ||
+        (r = download(tE, d_tE, size_t(cfg.n_train), st)) != ESP_OK)
+        return r;
+    double ss = 0.0;
+    for (int i = 0; i < cfg.n_train; ++i) {
+        tV[size_t(i)] -= tE[size_t(i)];
+        ss += tV[size_t(i)] * tV[size_t(i)];
     }
+    s->scale = std::max(std::sqrt(ss / std::max(cfg.n_train, 1)), 1e-300);
     std::vector<float> tgt(cfg.n_train);
     for (int i = 0; i < cfg.n_train; ++i)
-        tgt[size_t(i)] = float(base[size_t(i)] / s->scale);
+        tgt[size_t(i)] = float(tV[size_t(i)] / s->scale);
     DevBuf d_tgt;
     if ((e = upload_vec(d_tgt, tgt)) != cudaSuccess)
         return cuda_fail(e, "uploading training targets");
-    s->trust.assign(1, 0);
-    if ((r = init_device(s)) != ESP_OK)
-        return r;
     // training: mini-batches over the (already random) training set
     const int B = std::min(cfg.batch, cfg.n_train);
     if ((r = ensure_chunk(s, std::max(B, 1))) != ESP_OK)
@@ -586,7 +703,7 @@ esp_status train(esp_surrogate *s)
         double ep_loss = 0.0;
         for (int bi = 0; bi < steps_per_epoch; ++bi) {
             const int o = bi * B;
-            if ((r = forward(s, static_cast<const double *>(d_tpos.p) + 3 * size_t(o), B, st)) != ESP_OK ||
+            if ((r = forward(s, tp + 3 * size_t(o), B, st)) != ESP_OK ||
                 (r = output_layer(s, B, static_cast<const float *>(d_tgt.p) + o, st)) != ESP_OK ||
                 (r = backward(s, B, st)) != ESP_OK)
                 return r;
@@ -610,46 +727,86 @@ esp_status train(esp_surrogate *s)
         }
     }
     s->train_loss = last_loss;
+    s->packed = false; // the parameters changed: repack before the next inference
     if ((e = cudaMemcpy(s->params.data(), s->d_params.p, L.total * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "reading trained weights");
-    // validation errors and the trust map
-    if ((r = predict(s, static_cast<const double *>(d_vpos.p), cfg.n_valid, static_cast<double *>(d_vS.p), st)) != ESP_OK)
+    // validation of the far approximation against the exact far-tile sum, the
+    // expansion alone as the method without the network, and the trust map
+    if ((r = far_approx(s, vp, cfg.n_valid, static_cast<double *>(d_vS.p), false, st)) != ESP_OK)
         return r;
-    std::vector<double> vS(cfg.n_valid), err(cfg.n_valid);
-    if ((e = cudaMemcpy(vS.data(), d_vS.p, vS.size() * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_fail(e, "reading validation predictions");
-    if ((r = net_status(s)) != ESP_OK)
+    std::vector<double> vS, vV, vE;
+    if ((r = download(vS, d_vS, size_t(cfg.n_valid), st)) != ESP_OK || (r = net_status(s)) != ESP_OK ||
+        (r = download(vV, d_vV, size_t(cfg.n_valid), st)) != ESP_OK)
         return r;
-    double mx = 0.0, ss = 0.0, bmx = 0.0, bss = 0.0;
-    {
-        double P[3][kMaxDegree + 1];
-        for (int i = 0; i < cfg.n_valid; ++i) {
-            err[size_t(i)] = std::fabs(vS[size_t(i)] - vV[size_t(i)]);
-            mx = std::max(mx, err[size_t(i)]);
-            ss += err[size_t(i)] * err[size_t(i)];
-            for (int d = 0; d < 3; ++d)
-                legendre((vpos[size_t(i) * 3 + d] - s->centre[d]) * s->inv_r, s->degree, P[d]);
-            double b = 0.0;
-            for (int k = 0; k < s->ncoef; ++k)
-                b += s->coef[size_t(k)] * P[0][s->powers[3 * k]] * P[1][s->powers[3 * k + 1]] * P[2][s->powers[3 * k + 2]];
-            const double be = std::fabs(b - vV[size_t(i)]);
-            bmx = std::max(bmx, be);
-            bss += be * be;
-        }
+    if ((e = expansion(vp, cfg.n_valid, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p), s->degree,
+                       nullptr, 0.0, false, static_cast<double *>(d_vS.p), st)) != cudaSuccess)
+        return cuda_fail(e, "expansion at the validation positions");
+    if ((r = download(vE, d_vS, size_t(cfg.n_valid), st)) != ESP_OK)
+        return r;
+    std::vector<double> err(cfg.n_valid);
+    double mx = 0.0, sq = 0.0, bmx = 0.0, bsq = 0.0;
+    for (int i = 0; i < cfg.n_valid; ++i) {
+        err[size_t(i)] = std::fabs(vS[size_t(i)] - vV[size_t(i)]);
+        mx = std::max(mx, err[size_t(i)]);
+        sq += err[size_t(i)] * err[size_t(i)];
+        const double be = std::fabs(vE[size_t(i)] - vV[size_t(i)]);
+        bmx = std::max(bmx, be);
+        bsq += be * be;
     }
     s->valid_max_err = mx;
-    s->valid_rms_err = std::sqrt(ss / std::max(cfg.n_valid, 1));
+    s->valid_rms_err = std::sqrt(sq / std::max(cfg.n_valid, 1));
     s->base_max_err = bmx;
-    s->base_rms_err = std::sqrt(bss / std::max(cfg.n_valid, 1));
-    build_trust(s, vpos, err);
+    s->base_rms_err = std::sqrt(bsq / std::max(cfg.n_valid, 1));
+    if ((r = build_trust(s, vpos, err)) != ESP_OK)
+        return r;
     if ((e = upload_vec(s->d_trust, s->trust)) != cudaSuccess)
         return cuda_fail(e, "uploading the trust map");
-    d_tpos.release();
-    d_tV.release();
-    d_vpos.release();
-    d_vV.release();
-    d_vS.release();
-    d_tgt.release();
+    return ESP_OK;
+}
+
+esp_status ensure_fallback(esp_surrogate *s, int n)
+{
+    if (n <= s->fb_cap)
+        return ESP_OK;
+    cudaError_t e;
+    const int nb = (n + 1023) / 1024;
+    if ((e = s->d_flag.ensure(size_t(n) * 4)) != cudaSuccess || (e = s->d_pre.ensure(size_t(n) * 4)) != cudaSuccess ||
+        (e = s->d_tot.ensure(size_t(nb) * 4 + 4)) != cudaSuccess || (e = s->d_count.ensure(8)) != cudaSuccess ||
+        (e = s->d_cpos.ensure(size_t(n) * 24)) != cudaSuccess || (e = s->d_cidx.ensure(size_t(n) * 4)) != cudaSuccess ||
+        (e = s->d_cV.ensure(size_t(n) * 8)) != cudaSuccess || (e = s->d_nfail.ensure(8)) != cudaSuccess)
+        return cuda_fail(e, "allocating fallback buffers");
+    s->fb_cap = n;
+    return ESP_OK;
+}
+
+// Exact values (all tiles, FP32C) for the positions the trust map or the probe
+// selects; probes that miss tol withdraw their voxel (counted in d_nfail).
+// Returns the number of positions evaluated exactly.
+esp_status fallback_pass(esp_surrogate *s, const double *pos, int n, double *V, int stride, int *count_out)
+{
+    cudaStream_t st = s->ctx->stream;
+    cudaError_t e;
+    if ((e = fallback_select(pos, n, s->centre, s->cfg.voxel, s->dim, static_cast<const unsigned char *>(s->d_trust.p),
+                             stride, s->probe_offset, static_cast<int *>(s->d_flag.p), static_cast<int *>(s->d_pre.p),
+                             static_cast<int *>(s->d_tot.p), static_cast<int *>(s->d_count.p),
+                             static_cast<double *>(s->d_cpos.p), static_cast<int *>(s->d_cidx.p), st)) != cudaSuccess)
+        return cuda_fail(e, "selecting fallback positions");
+    int count = 0;
+    if ((e = cudaMemcpyAsync(&count, s->d_count.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "reading the fallback count");
+    *count_out = count;
+    if (count == 0)
+        return ESP_OK;
+    esp_status r = eval_view(s->ctx, s->ctx->full, 1, static_cast<const double *>(s->d_cpos.p), count,
+                             static_cast<double *>(s->d_cV.p));
+    if (r != ESP_OK)
+        return r;
+    if ((e = fallback_scatter(static_cast<const double *>(s->d_cV.p), static_cast<const int *>(s->d_cidx.p),
+                              static_cast<const int *>(s->d_count.p), count, V, pos, s->centre, s->cfg.voxel, s->dim,
+                              static_cast<unsigned char *>(s->d_trust.p), stride, s->probe_offset, s->cfg.tol,
+                              static_cast<int *>(s->d_nfail.p), st)) != cudaSuccess)
+        return cuda_fail(e, "merging fallback values");
     return ESP_OK;
 }
 
@@ -666,43 +823,28 @@ esp_status sur_eval(esp_surrogate *s, const double *pos, int64_t n64, double *V,
         return r;
     if ((e = cudaEventRecord(s->ev1, st)) != cudaSuccess)
         return cuda_fail(e, "recording surrogate events");
-    if (n > s->fb_cap) {
-        const int nb = (n + 1023) / 1024;
-        if ((e = s->d_flag.ensure(size_t(n) * 4)) != cudaSuccess || (e = s->d_pre.ensure(size_t(n) * 4)) != cudaSuccess ||
-            (e = s->d_tot.ensure(size_t(nb) * 4 + 4)) != cudaSuccess || (e = s->d_count.ensure(8)) != cudaSuccess ||
-            (e = s->d_cpos.ensure(size_t(n) * 24)) != cudaSuccess || (e = s->d_cidx.ensure(size_t(n) * 4)) != cudaSuccess ||
-            (e = s->d_cV.ensure(size_t(n) * 8)) != cudaSuccess || (e = s->d_nfail.ensure(8)) != cudaSuccess)
-            return cuda_fail(e, "allocating fallback buffers");
-        s->fb_cap = n;
-    }
-    const int stride = s->cfg.probe_stride;
-    if ((e = cudaMemsetAsync(s->d_nfail.p, 0, 4, st)) != cudaSuccess ||
-        (e = fallback_select(pos, n, s->centre, s->cfg.voxel, s->dim, static_cast<const unsigned char *>(s->d_trust.p),
-                             stride, s->probe_offset, static_cast<int *>(s->d_flag.p), static_cast<int *>(s->d_pre.p),
-                             static_cast<int *>(s->d_tot.p), static_cast<int *>(s->d_count.p),
-                             static_cast<double *>(s->d_cpos.p), static_cast<int *>(s->d_cidx.p), st)) != cudaSuccess)
-        return cuda_fail(e, "selecting fallback positions");
-    int count = 0, tc_err = 0;
-    if ((e = cudaMemcpyAsync(&count, s->d_count.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&tc_err, s->d_tcerr.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_fail(e, "reading the fallback count");
-    if (tc_err)
-        return fail(ESP_ERR_TIMEOUT, "surrogate network kernel: a bounded wait gave up");
-    if (count > 0) {
-        if ((r = esp_eval(ctx, static_cast<const double *>(s->d_cpos.p), count, static_cast<double *>(s->d_cV.p))) !=
-            ESP_OK)
-            return r;
-        if ((e = fallback_scatter(static_cast<const double *>(s->d_cV.p), static_cast<const int *>(s->d_cidx.p),
-                                  static_cast<const int *>(s->d_count.p), count, V, pos, s->centre, s->cfg.voxel,
-                                  s->dim, static_cast<unsigned char *>(s->d_trust.p), stride, s->probe_offset,
-                                  s->cfg.tol, static_cast<int *>(s->d_nfail.p), st)) != cudaSuccess)
-            return cuda_fail(e, "merging fallback values");
-    }
-    int nfail = 0;
-    if ((e = cudaEventRecord(s->ev2, st)) != cudaSuccess ||
+    if ((r = ensure_fallback(s, n)) != ESP_OK)
+        return r;
+    if ((e = cudaMemsetAsync(s->d_nfail.p, 0, 4, st)) != cudaSuccess)
+        return cuda_fail(e, "clearing the probe count");
+    int count = 0, tc_err = 0, nfail = 0;
+    if ((r = fallback_pass(s, pos, n, V, s->cfg.probe_stride, &count)) != ESP_OK)
+        return r;
+    if ((e = cudaMemcpyAsync(&tc_err, s->d_tcerr.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&nfail, s->d_nfail.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "reading the probe count");
+    if (tc_err)
+        return fail(ESP_ERR_TIMEOUT, "surrogate network kernel: a bounded wait gave up");
+    if (nfail > 0) {
+        // voxels withdrawn by this call's probes: their other positions of this
+        // call take the exact value too (no probes in this pass)
+        int again = 0;
+        if ((r = fallback_pass(s, pos, n, V, 0, &again)) != ESP_OK)
+            return r;
+        count += again;
+    }
+    if ((e = cudaEventRecord(s->ev2, st)) != cudaSuccess || (e = cudaEventSynchronize(s->ev2)) != cudaSuccess)
         return cuda_fail(e, "finishing the surrogate evaluation");
     float t1 = 0.f, t2 = 0.f;
     cudaEventElapsedTime(&t1, s->ev0, s->ev1);
@@ -711,8 +853,8 @@ esp_status sur_eval(esp_surrogate *s, const double *pos, int64_t n64, double *V,
     s->last_total_ms = t2;
     s->last_fallback = count;
     s->probe_fail_total += nfail;
-    if (stride > 0)
-        s->probe_offset = (s->probe_offset + 1) % stride;
+    if (s->cfg.probe_stride > 0)
+        s->probe_offset = (s->probe_offset + 1) % s->cfg.probe_stride;
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->n_fallback = count;
@@ -722,11 +864,13 @@ esp_status sur_eval(esp_surrogate *s, const double *pos, int64_t n64, double *V,
         stats->train_loss = s->train_loss;
         stats->valid_max_err = s->valid_max_err;
         stats->trusted_fraction = s->trusted_fraction;
+        stats->n_near_entries = s->n_near_entries;
+        stats->n_far_entries = s->n_far_entries;
     }
     return ESP_OK;
 }
 
-const uint32_t kFileMagic = 0x45535246u, kFileVersion = 1;
+const uint32_t kFileMagic = 0x45535246u, kFileVersion = 2;
 
 uint64_t checksum(const void *p, size_t n, uint64_t h)
 {
@@ -746,11 +890,11 @@ void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg)
         return;
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->size = int32_t(sizeof(esp_surrogate_cfg));
-    cfg->n_train = 1 << 22;
-    cfg->n_valid = 1 << 18;
-    cfg->epochs = 6;
+    cfg->n_train = 1 << 19;
+    cfg->n_valid = 1 << 17;
+    cfg->epochs = 8;
     cfg->batch = 8192;
-    cfg->degree = 10;
+    cfg->degree = 16;
     cfg->qm_radius = 6.0;
     cfg->position_sd = 2.0;
     cfg->fourier_sigma = 1.0;
@@ -759,7 +903,9 @@ void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg)
     cfg->voxel = 0.25;
     cfg->nucleus_exclusion = 0.5;
     cfg->probe_stride = 64;
+    cfg->label_precision = ESP_FP32C;
     cfg->seed = 1011;
+    cfg->far_radius = 12.0;
 }
 
 esp_status esp_surrogate_train(esp_ctx *ctx, const esp_surrogate_cfg *cfg_in, esp_surrogate **out)
@@ -777,11 +923,14 @@ esp_status esp_surrogate_train(esp_ctx *ctx, const esp_surrogate_cfg *cfg_in, es
         cfg = *cfg_in;
     }
     if (cfg.n_train < 1024 || cfg.n_valid < 64 || cfg.epochs < 0 || cfg.batch < 64 || cfg.degree < 0 ||
-        cfg.degree > kMaxDegree || !(cfg.qm_radius > 0.0) || !(cfg.voxel > 0.0) || !(cfg.tol > 0.0) ||
-        cfg.probe_stride < 0 || cfg.n_train > (1 << 26) || cfg.n_valid > (1 << 24))
+        cfg.degree > kMaxExpDegree || !(cfg.qm_radius > 0.0) || !(cfg.voxel > 0.0) || !(cfg.tol > 0.0) ||
+        cfg.probe_stride < 0 || cfg.n_train > (1 << 26) || cfg.n_valid > (1 << 24) ||
+        (cfg.label_precision != ESP_FP64 && cfg.label_precision != ESP_FP32C) ||
+        !(cfg.far_radius >= cfg.qm_radius) || !(cfg.far_radius < 1e6))
         return fail(ESP_ERR_INVALID, "bad surrogate configuration");
-    if (!ctx->host_copy)
-        return fail(ESP_ERR_UNSUPPORTED, "environment too large for the host copy the trust map needs");
+    BusyGuard busy(ctx->busy);
+    if (!busy.acquired)
+        return fail(ESP_ERR_STATE, "context is in use by another thread");
     esp_surrogate *s = new (std::nothrow) esp_surrogate();
     if (!s)
         return fail(ESP_ERR_OOM, "host allocation of the surrogate");
@@ -817,6 +966,9 @@ esp_status esp_surrogate_eval(esp_surrogate *s, const double *positions, int64_t
     DeviceGuard dg(s->ctx->device);
     if (classify(positions, s->ctx->device) != Space::Device || classify(V_out, s->ctx->device) != Space::Device)
         return fail(ESP_ERR_INVALID, "surrogate evaluation takes device memory");
+    BusyGuard busy(s->ctx->busy);
+    if (!busy.acquired)
+        return fail(ESP_ERR_STATE, "context is in use by another thread");
     return sur_eval(s, positions, n, V_out, stats);
 }
 
@@ -832,6 +984,9 @@ esp_status esp_surrogate_predict(esp_surrogate *s, const double *positions, int6
     DeviceGuard dg(s->ctx->device);
     if (classify(positions, s->ctx->device) != Space::Device || classify(V_out, s->ctx->device) != Space::Device)
         return fail(ESP_ERR_INVALID, "surrogate evaluation takes device memory");
+    BusyGuard busy(s->ctx->busy);
+    if (!busy.acquired)
+        return fail(ESP_ERR_STATE, "context is in use by another thread");
     esp_status r = predict(s, positions, int(n), V_out, s->ctx->stream);
     if (r != ESP_OK)
         return r;
@@ -856,6 +1011,8 @@ esp_status esp_surrogate_info(const esp_surrogate *s, esp_surrogate_stats *stats
     stats->valid_rms_err = s->valid_rms_err;
     stats->baseline_max_err = s->base_max_err;
     stats->baseline_rms_err = s->base_rms_err;
+    stats->n_near_entries = s->n_near_entries;
+    stats->n_far_entries = s->n_far_entries;
     return ESP_OK;
 }
 
@@ -913,6 +1070,23 @@ esp_status esp_surrogate_debug_net(esp_surrogate *s, const double *positions, in
     return ESP_OK;
 }
 
+esp_status esp_surrogate_debug_expansion(esp_surrogate *s, double dc, double *coef_out, int32_t max_coef)
+{
+    last_error().clear();
+    if (!valid_sur(s) || max_coef < 0 || (max_coef > 0 && !coef_out))
+        return fail(ESP_ERR_INVALID, "bad arguments");
+    if (dc != 0.0) {
+        DeviceGuard dg(s->ctx->device);
+        s->coef[0] += dc;
+        cudaError_t e = cudaMemcpy(s->d_coef.p, s->coef.data(), sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "updating the expansion");
+    }
+    for (int k = 0; k < std::min(max_coef, s->ncoef); ++k)
+        coef_out[k] = s->coef[size_t(k)];
+    return ESP_OK;
+}
+
 esp_status esp_surrogate_features(const esp_surrogate *s, float *freq_out, double *centre_inv_r_out)
 {
     if (!valid_sur(s) || !freq_out || !centre_inv_r_out)
@@ -938,12 +1112,11 @@ esp_status esp_surrogate_save(const esp_surrogate *s, const char *path)
     };
     int32_t hdr[8] = {int32_t(kFileMagic), int32_t(kFileVersion), s->degree, s->ncoef, s->dim, int32_t(layout().total),
                       kFreq, 0};
-    double dd[8] = {s->centre[0], s->centre[1], s->centre[2], s->inv_r, s->scale, s->train_loss, s->valid_max_err,
-                    s->trusted_fraction};
+    double dd[12] = {s->centre[0], s->centre[1], s->centre[2], s->inv_r, s->scale, s->train_loss, s->valid_max_err,
+                     s->trusted_fraction, s->valid_rms_err, s->base_max_err, s->base_rms_err, 0.0};
     bool ok = put(hdr, sizeof(hdr)) && put(dd, sizeof(dd)) && put(&s->cfg, sizeof(s->cfg)) &&
-              put(s->coef.data(), s->coef.size() * 8) && put(s->powers.data(), s->powers.size() * 4) &&
-              put(s->freq.data(), s->freq.size() * 4) && put(s->params.data(), s->params.size() * 4) &&
-              put(s->trust.data(), s->trust.size());
+              put(s->coef.data(), s->coef.size() * 8) && put(s->freq.data(), s->freq.size() * 4) &&
+              put(s->params.data(), s->params.size() * 4) && put(s->trust.data(), s->trust.size());
     ok = ok && std::fwrite(&h, 8, 1, f) == 1;
     ok = (std::fclose(f) == 0) && ok;
     return ok ? ESP_OK : fail(ESP_ERR_INVALID, "writing %s failed", path);
@@ -970,32 +1143,23 @@ esp_status esp_surrogate_load(esp_ctx *ctx, const char *path, esp_surrogate **ou
         return true;
     };
     int32_t hdr[8];
-    double dd[8];
+    double dd[12];
     bool ok = get(hdr, sizeof(hdr)) && uint32_t(hdr[0]) == kFileMagic && hdr[1] == int32_t(kFileVersion) &&
-              hdr[2] >= 0 && hdr[2] <= kMaxDegree && hdr[3] > 0 && hdr[3] < 100000 && hdr[4] > 0 && hdr[4] < 4096 &&
-              hdr[5] == int32_t(layout().total) && hdr[6] == kFreq && get(dd, sizeof(dd)) && get(&s->cfg, sizeof(s->cfg));
+              hdr[2] >= 0 && hdr[2] <= kMaxExpDegree && hdr[3] == num_harmonics(hdr[2]) && hdr[4] > 0 &&
+              hdr[4] < 4096 && hdr[5] == int32_t(layout().total) && hdr[6] == kFreq && get(dd, sizeof(dd)) &&
+              get(&s->cfg, sizeof(s->cfg)) && s->cfg.size == int32_t(sizeof(esp_surrogate_cfg));
     if (ok) {
         s->degree = hdr[2];
         s->ncoef = hdr[3];
         s->dim = hdr[4];
         s->coef.resize(size_t(s->ncoef));
-        s->powers.resize(size_t(s->ncoef) * 3);
         s->freq.resize(size_t(kFreq) * 3);
         s->params.resize(layout().total);
         s->trust.resize(size_t(s->dim) * s->dim * s->dim);
-        ok = get(s->coef.data(), s->coef.size() * 8) && get(s->powers.data(), s->powers.size() * 4) &&
-             get(s->freq.data(), s->freq.size() * 4) && get(s->params.data(), s->params.size() * 4) &&
-             get(s->trust.data(), s->trust.size());
+        ok = get(s->coef.data(), s->coef.size() * 8) && get(s->freq.data(), s->freq.size() * 4) &&
+             get(s->params.data(), s->params.size() * 4) && get(s->trust.data(), s->trust.size());
         uint64_t stored = 0;
         ok = ok && std::fread(&stored, 8, 1, f) == 1 && stored == h;
-        // the evaluation kernel walks the coefficients in the fit's (a, b, c) order
-        const int D = s->degree;
-        ok = ok && s->ncoef == (D + 1) * (D + 2) * (D + 3) / 6;
-        for (int a = 0, k = 0; ok && a <= D; ++a)
-            for (int b = 0; ok && a + b <= D; ++b)
-                for (int c = 0; ok && a + b + c <= D; ++c, ++k)
-                    ok = s->powers[3 * size_t(k)] == a && s->powers[3 * size_t(k) + 1] == b &&
-                         s->powers[3 * size_t(k) + 2] == c;
     }
     std::fclose(f);
     if (!ok) {
@@ -1009,7 +1173,12 @@ esp_status esp_surrogate_load(esp_ctx *ctx, const char *path, esp_surrogate **ou
     s->train_loss = dd[5];
     s->valid_max_err = dd[6];
     s->trusted_fraction = dd[7];
+    s->valid_rms_err = dd[8];
+    s->base_max_err = dd[9];
+    s->base_rms_err = dd[10];
     s->ctx = ctx;
+    // the near / far split is a function of the context's tiles and the configuration
+    split_tiles(s);
     DeviceGuard dg(ctx->device);
     esp_status st = init_device(s);
     if (st != ESP_OK) {

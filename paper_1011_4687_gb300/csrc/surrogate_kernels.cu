@@ -4,14 +4,15 @@
 // position u = (r - centre) / R (32 frequencies, 64 features), four hidden
 // layers of 256 with SiLU, one linear output.  BF16 weights and activations,
 // FP32 accumulation on the tensor cores (mma.sync m16n8k16), FP32 master
-// weights updated by Adam.  The network models the residual of an FP64
-// polynomial baseline (products of Legendre polynomials in u), so that its
-// BF16 output only has to carry a small correction.
+// weights updated by Adam.  The network models the residual of the far
+// environment's potential after its FP64 interior solid-harmonic expansion
+// (esp_harmonics.h), so that its BF16 output only carries a small correction.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
+#include "esp_harmonics.h"
 #include "surrogate_kernels.h"
 
 namespace esp {
@@ -250,57 +251,27 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, 
         wb[i] = __float2bfloat16(wi);
 }
 
-// V[i] = baseline(u) + scale * y[i] (FP64 baseline: sum_c coef[c] P_a(ux) P_b(uy) P_c(uz)).
-// The coefficients are in the fit's order (a, then b, then c ascending with
-// a + b + c <= degree; `powers` lists it), so the sum nests as
-// sum_a P_a(ux) sum_b P_b(uy) sum_c coef P_c(uz): one FMA per coefficient.
-// D > 0: the degree at compile time, so the Legendre values stay in registers;
-// D = 0: any degree (runtime loops).
-template <int D>
-__global__ void combine_kernel(const double *__restrict__ pos, int n, double cx, double cy, double cz,
-                               double inv_r, const double *__restrict__ coef, int degree_rt,
-                               const float *__restrict__ y, double scale, double *__restrict__ V)
+// Recursion constants of the solid harmonics (uniform across a warp: every
+// thread walks the same (l, m) sequence), set by set_harmonic_consts.
+__constant__ HarmonicConsts c_harm;
+
+// V[i] = (accumulate ? V[i] : 0) + sum_k coef[k] S_k(u_i) + scale * y[i]
+// (y may be null), u_i = (pos_i - centre) / R: the far field's FP64 interior
+// expansion plus the network's correction.
+__global__ void expansion_kernel(const double *__restrict__ pos, int n, double cx, double cy, double cz,
+                                 double inv_r, const double *__restrict__ coef, int L,
+                                 const float *__restrict__ y, double scale, int accumulate, double *__restrict__ V)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    const int degree = D > 0 ? D : degree_rt;
-    constexpr int kDim = (D > 0 ? D : kMaxDegree) + 1;
-    double u[3] = {(pos[3 * i] - cx) * inv_r, (pos[3 * i + 1] - cy) * inv_r, (pos[3 * i + 2] - cz) * inv_r};
-    double P[3][kDim];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        P[d][0] = 1.0;
-        if (degree >= 1)
-            P[d][1] = u[d];
-#pragma unroll
-        for (int l = 1; l < kDim - 1; ++l)
-            if (l < degree) // Bonnet: (l + 1) P_{l+1} = (2l + 1) u P_l - l P_{l-1}
-                P[d][l + 1] = ((2 * l + 1) * u[d] * P[d][l] - l * P[d][l - 1]) * (1.0 / (l + 1));
-    }
+    const double ux = (pos[3 * i] - cx) * inv_r, uy = (pos[3 * i + 1] - cy) * inv_r, uz = (pos[3 * i + 2] - cz) * inv_r;
     double s = 0.0;
-    int k = 0;
-#pragma unroll
-    for (int a = 0; a < kDim; ++a) {
-        if (a > degree)
-            break;
-        double sa = 0.0;
-#pragma unroll
-        for (int b = 0; a + b < kDim; ++b) {
-            if (a + b > degree)
-                break;
-            double sb = 0.0;
-#pragma unroll
-            for (int c = 0; a + b + c < kDim; ++c) {
-                if (a + b + c > degree)
-                    break;
-                sb = fma(__ldg(coef + k++), P[2][c], sb);
-            }
-            sa = fma(sb, P[1][b], sa);
-        }
-        s = fma(sa, P[0][a], s);
-    }
-    V[i] = s + scale * (double)y[i];
+    solid_harmonics(ux, uy, uz, L, c_harm.a, c_harm.b, c_harm.sec, c_harm.sub,
+                    [&](int k, double v) { s = fma(__ldg(coef + k), v, s); });
+    if (y)
+        s += scale * (double)y[i];
+    V[i] = accumulate ? V[i] + s : s;
 }
 
 // Fallback flags: untrusted voxel, outside the map, or probe position.
@@ -467,22 +438,26 @@ cudaError_t adam(float *w, const float *g, float *m, float *v, __nv_bfloat16 *wb
     return cudaGetLastError();
 }
 
-cudaError_t combine(const double *pos, int n, const double c[3], double inv_r, const double *coef, const int *powers,
-                    int ncoef, int degree, const float *y, double scale, double *V, cudaStream_t s)
+cudaError_t set_harmonic_consts()
+{
+    static HarmonicConsts h;
+    static bool ready = false;
+    if (!ready) {
+        harmonic_consts(h);
+        ready = true;
+    }
+    return cudaMemcpyToSymbol(c_harm, &h, sizeof(h));
+}
+
+cudaError_t expansion(const double *pos, int n, const double c[3], double inv_r, const double *coef, int L,
+                      const float *y, double scale, bool accumulate, double *V, cudaStream_t s)
 {
     if (n <= 0)
         return cudaSuccess;
-    (void)powers; // the kernel walks the fit's order itself (see combine_kernel)
-    (void)ncoef;
-    const dim3 grid((n + 127) / 128), block(128);
-    switch (degree) {
-    case 4: combine_kernel<4><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
-    case 6: combine_kernel<6><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
-    case 8: combine_kernel<8><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
-    case 10: combine_kernel<10><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
-    case 12: combine_kernel<12><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V); break;
-    default: combine_kernel<0><<<grid, block, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, degree, y, scale, V);
-    }
+    if (L < 0 || L > kMaxExpDegree)
+        return cudaErrorInvalidValue;
+    expansion_kernel<<<(n + 127) / 128, 128, 0, s>>>(pos, n, c[0], c[1], c[2], inv_r, coef, L, y, scale,
+                                                     accumulate ? 1 : 0, V);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,6 @@ constexpr int kFreq = 32;       // Fourier frequencies
 constexpr int kFeat = 64;       // features: sin and cos of each frequency
 constexpr int kHidden = 256;    // width of each hidden layer
 constexpr int kLayers = 4;      // hidden layers
-constexpr int kMaxDegree = 16;  // largest Legendre degree of the baseline
 
 enum { kEpiSiluFwd = 0, kEpiGradSilu = 1, kEpiRaw = 2 };
 
@@ -60,8 +59,14 @@ cudaError_t colsum(const __nv_bfloat16 *M, int n, float *part, int nparts, float
 cudaError_t sum_parts(const float *part, int nparts, int len, float *out, cudaStream_t s);
 cudaError_t adam(float *w, const float *g, float *m, float *v, __nv_bfloat16 *wb, int n, float lr, float b1,
                  float b2, int step, float eps, cudaStream_t s);
-cudaError_t combine(const double *pos, int n, const double c[3], double inv_r, const double *coef, const int *powers,
-                    int ncoef, int degree, const float *y, double scale, double *V, cudaStream_t s);
+// Recursion constants of the solid harmonics into the current device's
+// constant memory (once per device before the first expansion launch).
+cudaError_t set_harmonic_consts();
+// V[i] = (accumulate ? V[i] : 0) + sum_k coef[k] S_k(u_i) + scale * y[i]
+// (y may be null): the far field's interior expansion of degree L
+// (esp_harmonics.h) plus the network's correction, u_i = (pos_i - c) inv_r.
+cudaError_t expansion(const double *pos, int n, const double c[3], double inv_r, const double *coef, int L,
+                      const float *y, double scale, bool accumulate, double *V, cudaStream_t s);
 cudaError_t fallback_select(const double *pos, int n, const double c[3], double vox, int dim,
                             const unsigned char *trust, int probe_stride, int probe_offset, int *flag, int *pre,
                             int *tot, int *count, double *cpos, int *cidx, cudaStream_t s);

@@ -76,8 +76,8 @@ class SurrogateCfg(ctypes.Structure):
                 ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("degree", ctypes.c_int32),
                 ("qm_radius", ctypes.c_double), ("position_sd", ctypes.c_double), ("fourier_sigma", ctypes.c_double),
                 ("lr", ctypes.c_double), ("tol", ctypes.c_double), ("voxel", ctypes.c_double),
-                ("nucleus_exclusion", ctypes.c_double), ("probe_stride", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("nucleus_exclusion", ctypes.c_double), ("probe_stride", ctypes.c_int32),
+                ("label_precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("far_radius", ctypes.c_double)]
 
 
 class SurrogateStats(ctypes.Structure):
@@ -85,7 +85,8 @@ class SurrogateStats(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("train_loss", ctypes.c_double), ("valid_max_err", ctypes.c_double),
                 ("trusted_fraction", ctypes.c_double), ("n_params", ctypes.c_int64), ("n_baseline", ctypes.c_int64),
                 ("valid_rms_err", ctypes.c_double), ("baseline_max_err", ctypes.c_double),
-                ("baseline_rms_err", ctypes.c_double)]
+                ("baseline_rms_err", ctypes.c_double), ("n_near_entries", ctypes.c_int64),
+                ("n_far_entries", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -181,6 +182,10 @@ def load(build_if_missing: bool = False):
     lib.esp_surrogate_debug_step.restype = ctypes.c_int
     lib.esp_surrogate_features.argtypes = [P, P, P]
     lib.esp_surrogate_features.restype = ctypes.c_int
+    lib.esp_surrogate_debug_expansion.argtypes = [P, d, P, i32]
+    lib.esp_surrogate_debug_expansion.restype = ctypes.c_int
+    lib.esp_debug_solid_harmonics.argtypes = [i32, P, P]
+    lib.esp_debug_solid_harmonics.restype = ctypes.c_int
     lib.esp_surrogate_debug_net.argtypes = [P, P, i32, P]
     lib.esp_surrogate_debug_net.restype = ctypes.c_int
     lib.esp_surrogate_destroy.argtypes = [P]
@@ -374,6 +379,14 @@ def measure_peaks(device: int = -1) -> dict:
     return p.as_dict()
 
 
+def debug_solid_harmonics(L: int, u) -> np.ndarray:
+    """Test hook: the surrogate's real regular solid harmonics S_k(u), k < (L+1)^2, on the host."""
+    u = np.ascontiguousarray(u, np.float64).reshape(3)
+    out = np.zeros((L + 1) ** 2)
+    _check(load().esp_debug_solid_harmonics(int(L), u.ctypes.data, out.ctypes.data))
+    return out
+
+
 def debug_boys(precision, nmax: int, T: float) -> np.ndarray:
     """Test hook: the device Boys algorithm of `precision`, run on the host."""
     F = np.zeros(nmax + 1)
@@ -547,6 +560,13 @@ class Surrogate:
         y = np.zeros(pos.shape[0], np.float32)
         _check(load().esp_surrogate_debug_net(self._s, pos.ctypes.data, pos.shape[0], y.ctypes.data))
         return y
+
+    def debug_expansion(self, dc: float = 0.0) -> np.ndarray:
+        """Test hook: add dc to the expansion's constant coefficient; returns the coefficients."""
+        n = self.info()["n_baseline"]
+        c = np.zeros(max(n, 1))
+        _check(load().esp_surrogate_debug_expansion(self._s, float(dc), c.ctypes.data, int(n)))
+        return c[:n]
 
     def features(self):
         freq = np.zeros((32, 3), np.float32)

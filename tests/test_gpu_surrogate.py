@@ -1,8 +1,10 @@
 """The learned surrogate on the GPU: gradients of the library's BF16 tensor-core
-kernels against the CPU reference network, and the surrogate + exact-fallback
-contract against the FP64 oracle."""
+kernels against the CPU reference network, the fused inference kernel against
+that reference, and the surrogate's contract against the FP64 oracle: values
+served by expansion + network (not by the fallback) are checked element by
+element at 2e-6 Ha, walker energies at 1e-5 Ha, and a probe that fails makes
+its voxel's positions exact within the same call."""
 import functools
-import os
 
 import numpy as np
 import pytest
@@ -10,11 +12,12 @@ import pytest
 import oracle
 from oracle import mlp_reference as ref
 from paper_1011_4687_gb300 import build_lib, esp
-from workloads import qm_positions, small_environment
+from workloads import qm_positions, realistic_environment, small_environment
 
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
+WALKER_TOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -33,6 +36,9 @@ def env_small():
 
 
 def test_gradients_match_cpu_reference(torch):
+    """Every parameter's gradient against the FP64 reference network with the
+    kernels' BF16 rounding points, element by element: |g - g_ref| <= 2e-2 |g_ref|
+    + 2^-8 max|g_ref| of its block (BF16 keeps 8 significant bits)."""
     wl = env_small()
     env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs)
     with esp.Surrogate(env, n_train=2048, n_valid=512, epochs=0, degree=4) as sur:
@@ -49,17 +55,10 @@ def test_gradients_match_cpu_reference(torch):
         for name, off, shape in spec:
             n = int(np.prod(shape)) if shape else 1
             a, b = grad[off:off + n].astype(np.float64), gr[off:off + n]
-            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
-            assert rel <= 5e-2, (name, rel)
+            lim = 2e-2 * np.abs(b) + 2.0 ** -8 * np.abs(b).max()
+            bad = np.abs(a - b) > lim
+            assert not bad.any(), (name, int(bad.sum()), float((np.abs(a - b) / np.maximum(lim, 1e-300)).max()))
     env.close()
-
-
-@functools.lru_cache(maxsize=None)
-def trained(torch_mod):
-    wl = env_small()
-    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs)
-    sur = esp.Surrogate(env, n_train=1 << 17, n_valid=1 << 15, epochs=6, batch=4096)
-    return wl, env, sur
 
 
 def _check_fused_network(sur, pos):
@@ -90,27 +89,95 @@ def test_fused_network_matches_reference_untrained(torch):
     env.close()
 
 
+# ---------------------------------------------------------------------------
+# the realistic environment (2,000 atoms): near tiles exact, far tiles by
+# expansion + network
+# ---------------------------------------------------------------------------
+@functools.lru_cache(maxsize=None)
+def realistic():
+    return realistic_environment(seed=6602, n_atoms=2000, n_walkers=16, n_elec=32)
+
+
+_TRAINED = {}
+
+
+def trained(torch_mod):
+    if "sur" not in _TRAINED:
+        wl = realistic()
+        env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, stream=torch_mod.cuda.current_stream().cuda_stream)
+        sur = esp.Surrogate(env, n_train=1 << 18, n_valid=1 << 16, epochs=8)
+        _TRAINED.update(wl=wl, env=env, sur=sur)
+    return _TRAINED["wl"], _TRAINED["env"], _TRAINED["sur"]
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_at(n):
+    wl = realistic()
+    pos = np.concatenate([wl.positions, qm_positions(np.random.default_rng(90), n - wl.positions.shape[0])])
+    return pos, oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos)
+
+
 def test_fused_network_matches_reference_trained(torch):
     wl, env, sur = trained(torch)
     _check_fused_network(sur, qm_positions(np.random.default_rng(13), 4099))
 
 
-def test_surrogate_with_fallback_meets_tolerance(torch):
+def test_served_positions_match_oracle(torch):
+    """Positions the surrogate serves (expansion + network, no fallback) agree
+    with the FP64 oracle element by element at 2e-6 Ha; at least a third of the
+    positions are served; the 16 whole walkers meet 1e-5 Ha."""
     wl, env, sur = trained(torch)
     info = sur.info()
-    # the network improves on the baseline alone
-    assert info["valid_rms_err"] < info["baseline_rms_err"]
-    rng = np.random.default_rng(77)
-    pos = qm_positions(rng, 4096)
+    assert info["n_far_entries"] > 0 and info["n_near_entries"] > 0
+    assert info["trusted_fraction"] > 0.3, info
+    pos, ref_v = oracle_at(1024)
     V, st = sur.eval(torch.from_numpy(pos).cuda())
     torch.cuda.synchronize()
-    ref_v = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos)
-    assert np.abs(V.cpu().numpy() - ref_v).max() <= TOL
-    assert 0 < st["n_fallback"] <= pos.shape[0]
-    # a second call: the probe moves, results stay within tolerance
-    V2, st2 = sur.eval(torch.from_numpy(pos).cuda())
+    V = V.cpu().numpy()
+    # which positions were served: the trust map decides, plus every 64th probe
+    Vp = sur.predict(torch.from_numpy(pos).cuda())
     torch.cuda.synchronize()
-    assert np.abs(V2.cpu().numpy() - ref_v).max() <= TOL
+    served = V == Vp.cpu().numpy()
+    assert served.mean() >= 1.0 / 3.0, (served.mean(), st)
+    assert np.abs(V[served] - ref_v[served]).max() <= TOL
+    assert np.abs(V - ref_v).max() <= TOL
+    n = wl.n_walkers * wl.n_elec
+    E = -V[:n].reshape(wl.n_walkers, wl.n_elec).sum(1)
+    Eref = oracle.walker_energies(ref_v[:n], wl.n_walkers, wl.n_elec)
+    assert np.abs(E - Eref).max() <= WALKER_TOL
+
+
+def test_network_gains_over_expansion_alone(torch):
+    """The method without the network (the far field's expansion alone) against
+    the same with the network, on the validation set of the far field."""
+    wl, env, sur = trained(torch)
+    info = sur.info()
+    assert info["valid_rms_err"] < info["baseline_rms_err"], info
+    assert info["valid_max_err"] <= TOL / 2 or info["trusted_fraction"] < 1.0
+
+
+def test_failed_probe_makes_its_voxel_exact_in_the_same_call(torch, tmp_path):
+    """A planted error (1e-3 Ha added to the expansion) fails every probe; the
+    positions are laid out 64 to a voxel, so every voxel holds one probe of the
+    call, and every returned value must still meet 2e-6 against the oracle."""
+    wl, env, sur = trained(torch)
+    path = str(tmp_path / "sur.bin")
+    sur.save(path)
+    other = esp.Surrogate.load(env, path)
+    try:
+        vox = 0.25
+        rng = np.random.default_rng(91)
+        centres = qm_positions(rng, 12, sd=1.5)
+        centres = (np.floor(centres / vox) + 0.5) * vox
+        pos = np.concatenate([c + rng.uniform(-0.45 * vox, 0.45 * vox, size=(64, 3)) for c in centres])
+        ref_v = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos)
+        other.debug_expansion(1e-3)
+        V, st = other.eval(torch.from_numpy(pos).cuda())
+        torch.cuda.synchronize()
+        assert st["n_probe_fail"] > 0
+        assert np.abs(V.cpu().numpy() - ref_v).max() <= TOL
+    finally:
+        other.close()
 
 
 def test_save_load_round_trip(torch, tmp_path):
