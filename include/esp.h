@@ -436,10 +436,11 @@ esp_status esp_work_census(esp_ctx *ctx, const double *positions, int64_t n, int
  * ------------------------------------------------------------------------ */
 typedef struct {
     double fp32_fma_per_s;    /* FFMA lane ops / s */
+    double fp32x2_fma_per_s;  /* FP32 FMA lane ops / s issued as packed pairs (FFMA2, two per instruction) */
     double fp64_fma_per_s;    /* DFMA lane ops / s */
     double mufu_rsqrt_per_s;  /* MUFU reciprocal square root, lane ops / s */
     double mufu_ex2_per_s;    /* MUFU base-2 exponential, lane ops / s */
-    double fp32_ms, fp64_ms, rsqrt_ms, ex2_ms; /* duration of one timed launch */
+    double fp32_ms, fp32x2_ms, fp64_ms, rsqrt_ms, ex2_ms; /* duration of one timed launch */
     int32_t num_sms;          /* cudaDevAttrMultiProcessorCount of the device */
     int32_t clock_khz;        /* cudaDevAttrClockRate (the rated, not the live clock) */
 } esp_peaks;

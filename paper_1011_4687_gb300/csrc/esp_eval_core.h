@@ -209,6 +209,103 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
     }
 }
 
+// Paired form of tile_f32c for the kernel: NP pairs of positions, each pair
+// held as two FP32 lanes (f2) so that every FP32 operation of the two
+// positions is one packed instruction.  Lane by lane it performs the
+// operations of tile_f32c in the same order; positions flagged near take a
+// zero weight (wq = 0) instead of a select.
+ESP_HD void two_sum_acc(f2 &S, f2 &C, f2 x)
+{
+    f2 s = S + x;
+    f2 bp = s - S;
+    f2 e = (S - (s - bp)) + (x - bp);
+    S = s;
+    C += e;
+}
+
+template <int L, int NP, bool FAR, bool SHORT, bool SEL>
+ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP][3], const f2 (&cl)[NP][3],
+                       const f2 (&wq)[NP], f2 (&S)[NP], f2 (&Cc)[NP], const float *__restrict__ s_boys)
+{
+    constexpr int st = rec32_stride(L);
+    constexpr int nh = num_hermite(L);
+    constexpr int co = FAR ? rec32_m(L) : rec32_g(L);
+    constexpr int c0lo = FAR ? rec32_lo(L) + 3 : rec32_g0lo(L);
+    auto one = [&](int j, f2 (&blk)[NP]) {
+        const float *r = s_rec + j * st;
+        const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
+        const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
+        const f2 px(r0.x), py(r0.y), pz(r0.z);
+        const f2 plx(r1.x), ply(r1.y), plz(r1.z);
+        const float ps = r0.w;
+        const float k0lo = FAR ? r1.w : r[c0lo];
+        float K[nh];
+        if constexpr (FAR) {
+#pragma unroll
+            for (int h = 0; h + 3 < nh; h += 4) {
+                const float4 k4 = reinterpret_cast<const float4 *>(r + co)[h / 4];
+                K[h] = k4.x;
+                K[h + 1] = k4.y;
+                K[h + 2] = k4.z;
+                K[h + 3] = k4.w;
+            }
+#pragma unroll
+            for (int h = nh - nh % 4; h < nh; ++h)
+                K[h] = r[co + h];
+        } else {
+#pragma unroll
+            for (int h = 0; h < nh; ++h)
+                K[h] = r[co + h];
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const f2 dx = (px - ch[q][0]) + (plx - cl[q][0]);
+            const f2 dy = (py - ch[q][1]) + (ply - cl[q][1]);
+            const f2 dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+            f2 v;
+            f2 F[L + 1];
+            if constexpr (FAR) {
+                const f2 r2 = esp_fma(dx, dx, esp_fma(dy, dy, dz * dz));
+                boys_far<L, f2>(r2, F);
+                v = hermite_contract<L, f2, float>(F, dx, dy, dz, K, k0lo);
+            } else if constexpr (L == 0) {
+                const f2 r2 = esp_fma(dx, dx, esp_fma(dy, dy, dz * dz));
+                const f2 T = esp_fma(f2(ps), r2, f2(r[rec32_pslo(L)]) * r2);
+                if constexpr (SHORT)
+                    F[0] = boys_f0_short(T);
+                else
+                    boys_eval<L>(T, s_boys, F);
+                v = hermite_contract<L, f2, float>(F, dx, dy, dz, K, k0lo);
+            } else {
+                const f2 sp(ps), pslo(r[rec32_pslo(L)]);
+                const f2 x = esp_fma(sp, dx, pslo * dx), y = esp_fma(sp, dy, pslo * dy),
+                         z = esp_fma(sp, dz, pslo * dz);
+                const f2 T = esp_fma(x, x, esp_fma(y, y, z * z));
+                boys_eval<L>(T, s_boys, F);
+                if constexpr (SHORT)
+                    F[0] = boys_f0_short(T);
+                v = hermite_contract<L, f2, float>(F, x, y, z, K, k0lo);
+            }
+            if constexpr (SEL)
+                blk[q] = esp_fma(v, wq[q], blk[q]);
+            else
+                blk[q] += v;
+        }
+    };
+    for (int j0 = 0; j0 < n; j0 += kSumBlock) {
+        f2 blk[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            blk[q] = f2(0.0f);
+        const int j1 = (j0 + kSumBlock < n) ? j0 + kSumBlock : n;
+        for (int j = j0; j < j1; ++j)
+            one(j, blk);
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            two_sum_acc(S[q], Cc[q], blk[q]);
+    }
+}
+
 // Per-position classification of a tile: near (FP64 instead; only with a
 // positive near_r and for tiles whose distributions can produce potentials
 // above kNearVmax) and far (the asymptotic form is exact to FP32 for every

@@ -123,6 +123,44 @@ template <> struct BoysConst<double> {
     ESP_HD static double tmax() { return kBoys64Tmax; }
 };
 
+ESP_HD float esp_fma(float a, float b, float c) { return fmaf(a, b, c); }
+ESP_HD double esp_fma(double a, double b, double c) { return fma(a, b, c); }
+
+// ---------------------------------------------------------------------------
+// Two FP32 lanes (two positions) per value.  On sm_100 and later every
+// operation is one packed instruction (FADD2 / FMUL2 / FFMA2) that does both
+// lanes, which halves the FP32 instructions the potential kernel issues; each
+// lane rounds exactly as the scalar operation would.  Host code (test hooks)
+// computes the lanes one after the other.
+// ---------------------------------------------------------------------------
+struct f2 {
+    float x, y;
+    ESP_HD f2() = default;
+    ESP_HD constexpr f2(float a, float b) : x(a), y(b) {}
+    ESP_HD constexpr explicit f2(float a) : x(a), y(a) {}
+};
+#if defined(__CUDA_ARCH__)
+ESP_HD float2 f2_v(f2 a) { return make_float2(a.x, a.y); }
+ESP_HD f2 v_f2(float2 a) { return f2(a.x, a.y); }
+ESP_HD f2 operator+(f2 a, f2 b) { return v_f2(__fadd2_rn(f2_v(a), f2_v(b))); }
+ESP_HD f2 operator-(f2 a, f2 b) { return v_f2(__fadd2_rn(f2_v(a), make_float2(-b.x, -b.y))); }
+ESP_HD f2 operator*(f2 a, f2 b) { return v_f2(__fmul2_rn(f2_v(a), f2_v(b))); }
+ESP_HD f2 esp_fma(f2 a, f2 b, f2 c) { return v_f2(__ffma2_rn(f2_v(a), f2_v(b), f2_v(c))); }
+#else
+ESP_HD f2 operator+(f2 a, f2 b) { return f2(a.x + b.x, a.y + b.y); }
+ESP_HD f2 operator-(f2 a, f2 b) { return f2(a.x - b.x, a.y - b.y); }
+ESP_HD f2 operator*(f2 a, f2 b) { return f2(a.x * b.x, a.y * b.y); }
+ESP_HD f2 esp_fma(f2 a, f2 b, f2 c) { return f2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
+#endif
+ESP_HD f2 operator-(f2 a) { return f2(-a.x, -a.y); }
+ESP_HD f2 &operator+=(f2 &a, f2 b) { return a = a + b; }
+ESP_HD f2 esp_fma(float a, f2 b, f2 c) { return esp_fma(f2(a), b, c); }
+ESP_HD f2 operator*(float a, f2 b) { return f2(a) * b; }
+
+// Scalar type of a lane: float for f2.
+template <typename R> struct lane_of { using type = R; };
+template <> struct lane_of<f2> { using type = float; };
+
 ESP_HD float esp_rsqrt(float x)
 {
 #if defined(__CUDA_ARCH__)
@@ -135,6 +173,18 @@ ESP_HD float esp_rsqrt(float x)
     float e = fmaf(-h, y, 1.0f);
     return fmaf(0.5f * e, y, y);
 }
+ESP_HD f2 esp_rsqrt(f2 x)
+{
+#if defined(__CUDA_ARCH__)
+    f2 y(rsqrtf(x.x), rsqrtf(x.y));
+#else
+    f2 y(1.0f / sqrtf(x.x), 1.0f / sqrtf(x.y));
+#endif
+    // the scalar version's Newton step, both lanes per instruction
+    f2 h = x * y;
+    f2 e = esp_fma(-h, y, f2(1.0f));
+    return esp_fma(f2(0.5f) * e, y, y);
+}
 ESP_HD double esp_rsqrt(double x)
 {
 #if defined(__CUDA_ARCH__)
@@ -144,8 +194,6 @@ ESP_HD double esp_rsqrt(double x)
 #endif
 }
 
-ESP_HD float esp_fma(float a, float b, float c) { return fmaf(a, b, c); }
-ESP_HD double esp_fma(double a, double b, double c) { return fma(a, b, c); }
 
 // x * k with the constant k carried as hi + lo words, rounded once:
 // fma(x, hi, x * lo).  Adding x * lo after rounding x * hi would be lost to
@@ -153,11 +201,12 @@ ESP_HD double esp_fma(double a, double b, double c) { return fma(a, b, c); }
 template <typename R>
 ESP_HD R mul_const(R x, double k)
 {
-    const R hi = R(k);
-    const R lo = R(k - double(hi));
-    if (lo == R(0)) // k exact in R (folded at compile time for constant k)
-        return x * hi;
-    return esp_fma(x, hi, x * lo);
+    using S = typename lane_of<R>::type;
+    const S hi = S(k);
+    const S lo = S(k - double(hi));
+    if (lo == S(0)) // k exact in R (folded at compile time for constant k)
+        return x * R(hi);
+    return esp_fma(x, R(hi), x * R(lo));
 }
 
 template <int L, typename R>
@@ -205,6 +254,54 @@ ESP_HD void boys_eval(R T, const R *__restrict__ tab, R (&F)[L + 1])
     }
 }
 
+// Both lanes of a pair: the asymptotic form when both lanes are at or above
+// Tmax, the table when both are below, else each lane by the scalar code.
+template <int L>
+ESP_HD void boys_eval(f2 T, const float *__restrict__ tab, f2 (&F)[L + 1])
+{
+    using C = BoysConst<float>;
+    const bool a0 = T.x >= C::tmax(), a1 = T.y >= C::tmax();
+    if (a0 && a1) {
+        f2 rs = esp_rsqrt(T);
+        F[0] = mul_const(rs, 0.88622692545275801365);
+        f2 h = f2(0.5f) * rs * rs;
+#pragma unroll
+        for (int n = 1; n <= L; ++n)
+            F[n] = F[n - 1] * (f2(float(2 * n - 1)) * h);
+    } else if (!a0 && !a1) {
+        const int i0 = (int)(T.x * 8.0f + 0.5f), i1 = (int)(T.y * 8.0f + 0.5f);
+        const f2 d = T - f2(float(i0) * 0.125f, float(i1) * 0.125f); // exact: |T - T_i| <= 1/16
+        const float *r0 = tab + i0 * C::kRow, *r1 = tab + i1 * C::kRow;
+        const f2 md = -d;
+        f2 f(r0[L + C::kTerms - 1], r1[L + C::kTerms - 1]);
+#pragma unroll
+        for (int k = C::kTerms - 2; k >= 1; --k)
+            f = esp_fma(f, md * f2(float(1.0 / (k + 1))), f2(r0[L + k], r1[L + k]));
+        f = f * md;
+        F[L] = f2(r0[L], r1[L]) + (f2(r0[kBoys32LoCol + L], r1[kBoys32LoCol + L]) + f);
+        if constexpr (L > 0) {
+            f2 q(1.0f);
+#pragma unroll
+            for (int k = C::kTerms; k >= 2; --k)
+                q = esp_fma(q, md * f2(float(1.0 / k)), f2(1.0f));
+            q = q * md;
+            const f2 ex(r0[C::kExpCol], r1[C::kExpCol]);
+            const f2 e = ex + esp_fma(ex, q, f2(r0[kBoys32LoCol + 5], r1[kBoys32LoCol + 5]));
+            const f2 T2 = T + T;
+#pragma unroll
+            for (int n = L - 1; n >= 0; --n)
+                F[n] = mul_const(esp_fma(T2, F[n + 1], e), 1.0 / (2 * n + 1));
+        }
+    } else {
+        float G0[L + 1], G1[L + 1];
+        boys_eval<L, float>(T.x, tab, G0);
+        boys_eval<L, float>(T.y, tab, G1);
+#pragma unroll
+        for (int n = 0; n <= L; ++n)
+            F[n] = f2(G0[n], G1[n]);
+    }
+}
+
 ESP_HD float esp_erfc(float x) { return erfcf(x); }
 ESP_HD double esp_erfc(double x) { return erfc(x); }
 
@@ -219,6 +316,8 @@ ESP_HD R boys_f0_short(R T)
     R rs = esp_rsqrt(T);
     return -mul_const(esp_erfc(T * rs) * rs, 0.88622692545275801365);
 }
+
+ESP_HD f2 boys_f0_short(f2 T) { return f2(boys_f0_short<float>(T.x), boys_f0_short<float>(T.y)); }
 
 // Far-field Boys values in units of sqrt(pi)/2 and for unit exponent:
 // Fh_0 = 1/sqrt(r2), Fh_n = Fh_{n-1} (2n-1) / (2 r2).  With these, the
@@ -241,8 +340,8 @@ ESP_HD void boys_far(R r2, R (&F)[L + 1])
 // scaled offset (x, y, z) = sqrt(p) (P - C), given F_0..F_L(T).
 // ---------------------------------------------------------------------------
 // g0lo is the low word of G_0: the leading product is rounded once with it.
-template <int L, typename R>
-ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const R *__restrict__ G, R g0lo = R(0))
+template <int L, typename R, typename G_t = R>
+ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const G_t *__restrict__ G, G_t g0lo = G_t(0))
 {
     if constexpr (L == 0) {
         return esp_fma(G[0], F[0], g0lo * F[0]);
@@ -267,15 +366,15 @@ ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const R *__restric
                     if (t > 0) {
                         val = x * S[n + 1][hidx(t - 1, u, v)];
                         if (t > 1)
-                            val += R(t - 1) * S[n + 1][hidx(t - 2, u, v)];
+                            val = esp_fma(R(t - 1), S[n + 1][hidx(t - 2, u, v)], val);
                     } else if (u > 0) {
                         val = y * S[n + 1][hidx(t, u - 1, v)];
                         if (u > 1)
-                            val += R(u - 1) * S[n + 1][hidx(t, u - 2, v)];
+                            val = esp_fma(R(u - 1), S[n + 1][hidx(t, u - 2, v)], val);
                     } else {
                         val = z * S[n + 1][hidx(t, u, v - 1)];
                         if (v > 1)
-                            val += R(v - 1) * S[n + 1][hidx(t, u, v - 2)];
+                            val = esp_fma(R(v - 1), S[n + 1][hidx(t, u, v - 2)], val);
                     }
                     S[n][hidx(t, u, v)] = val;
                 }

@@ -60,6 +60,20 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         Cc[q] = 0.0f;
         acc64[q] = 0.0;
     }
+    // the same positions as lane pairs (used when PPT is even)
+    constexpr int NP = PPT / 2 > 0 ? PPT / 2 : 1;
+    f2 ch2[NP][3], cl2[NP][3], S2[NP], C2[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int q0 = 2 * q < PPT ? 2 * q : 0, q1 = 2 * q + 1 < PPT ? 2 * q + 1 : 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ch2[q][d] = f2(ch[q0][d], ch[q1][d]);
+            cl2[q][d] = f2(cl[q0][d], cl[q1][d]);
+        }
+        S2[q] = f2(0.0f);
+        C2[q] = f2(0.0f);
+    }
     const float near_r = a.near_r;
     // this split's group and its place among the group's splits
     int g = 0;
@@ -100,6 +114,36 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         const bool far = __all_sync(0xffffffffu, lane_far);
         const bool sel = __any_sync(0xffffffffu, any_near); // warp-uniform: any term to select away
         const float *s_rec = reinterpret_cast<const float *>(s_tile4);
+        if constexpr (PPT % 2 == 0) {
+            // two positions per packed FP32 instruction
+            f2 wq[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                wq[q] = f2(nearq[2 * q] ? 0.0f : 1.0f, nearq[2 * q + 1] ? 0.0f : 1.0f);
+#define ESP_TILE(CLS, LL, SH)                                                                   \
+    case CLS:                                                                                   \
+        if (far && !sel)                                                                        \
+            tile_f32c2<LL, NP, true, SH, false>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);      \
+        else if (far)                                                                           \
+            tile_f32c2<LL, NP, true, SH, true>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);       \
+        else                                                                                    \
+            tile_f32c2<LL, NP, false, SH, true>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);      \
+        break;
+            switch (m.cls) {
+                ESP_TILE(0, 0, false)
+                ESP_TILE(1, 1, false)
+                ESP_TILE(2, 2, false)
+                ESP_TILE(3, 3, false)
+                ESP_TILE(4, 4, false)
+                ESP_TILE(8, 0, true)
+                ESP_TILE(9, 1, true)
+                ESP_TILE(10, 2, true)
+                ESP_TILE(11, 3, true)
+                default:
+                ESP_TILE(12, 4, true)
+            }
+#undef ESP_TILE
+        } else {
 #define ESP_TILE(CLS, LL, SH)                                                                   \
     case CLS:                                                                                   \
         if (far && !sel)                                                                        \
@@ -109,20 +153,21 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         else                                                                                    \
             tile_f32c<LL, PPT, false, SH, true>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);      \
         break;
-        switch (m.cls) {
-            ESP_TILE(0, 0, false)
-            ESP_TILE(1, 1, false)
-            ESP_TILE(2, 2, false)
-            ESP_TILE(3, 3, false)
-            ESP_TILE(4, 4, false)
-            ESP_TILE(8, 0, true)
-            ESP_TILE(9, 1, true)
-            ESP_TILE(10, 2, true)
-            ESP_TILE(11, 3, true)
-            default:
-            ESP_TILE(12, 4, true)
-        }
+            switch (m.cls) {
+                ESP_TILE(0, 0, false)
+                ESP_TILE(1, 1, false)
+                ESP_TILE(2, 2, false)
+                ESP_TILE(3, 3, false)
+                ESP_TILE(4, 4, false)
+                ESP_TILE(8, 0, true)
+                ESP_TILE(9, 1, true)
+                ESP_TILE(10, 2, true)
+                ESP_TILE(11, 3, true)
+                default:
+                ESP_TILE(12, 4, true)
+            }
 #undef ESP_TILE
+        }
         if (any_near) {
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
@@ -134,6 +179,15 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
             }
         }
     }
+    if constexpr (PPT % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            S[2 * q] = S2[q].x;
+            S[2 * q + 1] = S2[q].y;
+            Cc[2 * q] = C2[q].x;
+            Cc[2 * q + 1] = C2[q].y;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < PPT; ++q)
         if (idx[q] < a.n_pos)
@@ -141,7 +195,7 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
 }
 
 template <int NT, int PPT>
-__global__ void __launch_bounds__(NT) potential_f32c_kernel(EvalArgs a)
+__global__ void __launch_bounds__(NT, 512 / NT) potential_f32c_kernel(EvalArgs a)
 {
     extern __shared__ float4 smem4[];
     float4 *s_tile4 = smem4;
@@ -270,7 +324,7 @@ __device__ __forceinline__ EvalArgs args_of(const SysDesc &d, const float *boys3
 }
 
 template <int NT, int PPT, int PREC>
-__global__ void __launch_bounds__(NT) batch_potential_kernel(const BatchHeader *__restrict__ hdr,
+__global__ void __launch_bounds__(NT, PREC == 1 ? 512 / NT : 1) batch_potential_kernel(const BatchHeader *__restrict__ hdr,
                                                              const SysDesc *__restrict__ sys, int *counter,
                                                              const float *boys32, const double *boys64,
                                                              int tile_cap)

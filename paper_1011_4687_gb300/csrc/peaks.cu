@@ -45,6 +45,30 @@ __global__ void __launch_bounds__(kThreads) ffma_kernel(float *out, int iters, f
         out[blockIdx.x] = acc;
 }
 
+// Packed FP32 pairs (sm_100 and later): one instruction does two lanes' FMAs.
+__global__ void __launch_bounds__(kThreads) ffma2_kernel(float *out, int iters, float a, float b)
+{
+    float2 x[kChains / 2];
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k)
+        x[k] = make_float2(float(threadIdx.x + k) * 1e-3f, float(threadIdx.x + 2 * k) * 1e-3f);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int k = 0; k < kChains / 2; ++k)
+                x[k] = __ffma2_rn(x[k], a2, b2);
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k)
+        acc += x[k].x + x[k].y;
+    if (acc == 12345.678f)
+        out[blockIdx.x] = acc;
+}
+
 __global__ void __launch_bounds__(kThreads) dfma_kernel(double *out, int iters, double a, double b)
 {
     double x[kChains / 2];
@@ -185,6 +209,9 @@ extern "C" esp_status esp_measure_peaks(int32_t device, esp_peaks *out)
     const int it32 = 4096, it64 = 64, itmufu = 512;
     esp_status st = time_rate([&] { ffma_kernel<<<grid, kThreads>>>(scratch, it32, 0.999f, 1e-3f); },
                               lanes * it32 * 8 * kChains, 5, &p.fp32_fma_per_s, &p.fp32_ms);
+    if (st == ESP_OK)
+        st = time_rate([&] { ffma2_kernel<<<grid, kThreads>>>(scratch, it32, 0.999f, 1e-3f); },
+                       lanes * it32 * 8 * kChains, 5, &p.fp32x2_fma_per_s, &p.fp32x2_ms);
     if (st == ESP_OK)
         st = time_rate([&] { dfma_kernel<<<grid, kThreads>>>(reinterpret_cast<double *>(scratch), it64, 0.999, 1e-3); },
                        lanes * it64 * 8 * (kChains / 2), 5, &p.fp64_fma_per_s, &p.fp64_ms);

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -93,9 +94,11 @@ class SurrogateStats(ctypes.Structure):
 
 
 class Peaks(ctypes.Structure):
-    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double),
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp32x2_fma_per_s", ctypes.c_double),
+                ("fp64_fma_per_s", ctypes.c_double),
                 ("mufu_rsqrt_per_s", ctypes.c_double), ("mufu_ex2_per_s", ctypes.c_double),
-                ("fp32_ms", ctypes.c_double), ("fp64_ms", ctypes.c_double), ("rsqrt_ms", ctypes.c_double),
+                ("fp32_ms", ctypes.c_double), ("fp32x2_ms", ctypes.c_double), ("fp64_ms", ctypes.c_double),
+                ("rsqrt_ms", ctypes.c_double),
                 ("ex2_ms", ctypes.c_double), ("num_sms", ctypes.c_int32), ("clock_khz", ctypes.c_int32)]
 
     def as_dict(self):
@@ -274,9 +277,13 @@ class Environment:
                               pr.size, ctypes.byref(opt), ctypes.byref(ctx)))
         self._ctx = ctx
         self.stream = stream
+        self._dependents = weakref.WeakSet()  # surrogates bound to this context
 
     # -- lifetime ------------------------------------------------------------
     def close(self):
+        """Free the context (and first any surrogate still bound to it)."""
+        for d in list(getattr(self, "_dependents", ())):
+            d.close()
         if getattr(self, "_ctx", None) and self._ctx.value:
             load().esp_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
@@ -499,6 +506,7 @@ class Surrogate:
         self.env = env
         if _handle is not None:
             self._s = _handle
+            env._dependents.add(self)
             return
         lib = load()
         c = SurrogateCfg()
@@ -508,6 +516,7 @@ class Surrogate:
         h = ctypes.c_void_p()
         _check(lib.esp_surrogate_train(env.handle, ctypes.byref(c), ctypes.byref(h)))
         self._s = h
+        env._dependents.add(self)
 
     @staticmethod
     def load(env, path):

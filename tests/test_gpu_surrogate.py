@@ -98,16 +98,16 @@ def realistic():
     return realistic_environment(seed=6602, n_atoms=2000, n_walkers=16, n_elec=32)
 
 
-_TRAINED = {}
-
-
-def trained(torch_mod):
-    if "sur" not in _TRAINED:
-        wl = realistic()
-        env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, stream=torch_mod.cuda.current_stream().cuda_stream)
-        sur = esp.Surrogate(env, n_train=1 << 18, n_valid=1 << 16, epochs=8)
-        _TRAINED.update(wl=wl, env=env, sur=sur)
-    return _TRAINED["wl"], _TRAINED["env"], _TRAINED["sur"]
+@pytest.fixture(scope="module")
+def trained_sur(torch):
+    """One surrogate of the realistic environment for the tests below; closed
+    (surrogate first, then its environment) when the module's tests end."""
+    wl = realistic()
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs)
+    sur = esp.Surrogate(env, n_train=1 << 18, n_valid=1 << 16, epochs=8)
+    yield wl, env, sur
+    sur.close()
+    env.close()
 
 
 @functools.lru_cache(maxsize=None)
@@ -117,16 +117,16 @@ def oracle_at(n):
     return pos, oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, pos)
 
 
-def test_fused_network_matches_reference_trained(torch):
-    wl, env, sur = trained(torch)
+def test_fused_network_matches_reference_trained(trained_sur):
+    wl, env, sur = trained_sur
     _check_fused_network(sur, qm_positions(np.random.default_rng(13), 4099))
 
 
-def test_served_positions_match_oracle(torch):
+def test_served_positions_match_oracle(torch, trained_sur):
     """Positions the surrogate serves (expansion + network, no fallback) agree
     with the FP64 oracle element by element at 2e-6 Ha; at least a third of the
     positions are served; the 16 whole walkers meet 1e-5 Ha."""
-    wl, env, sur = trained(torch)
+    wl, env, sur = trained_sur
     info = sur.info()
     assert info["n_far_entries"] > 0 and info["n_near_entries"] > 0
     assert info["trusted_fraction"] > 0.3, info
@@ -147,20 +147,20 @@ def test_served_positions_match_oracle(torch):
     assert np.abs(E - Eref).max() <= WALKER_TOL
 
 
-def test_network_gains_over_expansion_alone(torch):
+def test_network_gains_over_expansion_alone(trained_sur):
     """The method without the network (the far field's expansion alone) against
     the same with the network, on the validation set of the far field."""
-    wl, env, sur = trained(torch)
+    wl, env, sur = trained_sur
     info = sur.info()
     assert info["valid_rms_err"] < info["baseline_rms_err"], info
     assert info["valid_max_err"] <= TOL / 2 or info["trusted_fraction"] < 1.0
 
 
-def test_failed_probe_makes_its_voxel_exact_in_the_same_call(torch, tmp_path):
+def test_failed_probe_makes_its_voxel_exact_in_the_same_call(torch, trained_sur, tmp_path):
     """A planted error (1e-3 Ha added to the expansion) fails every probe; the
     positions are laid out 64 to a voxel, so every voxel holds one probe of the
     call, and every returned value must still meet 2e-6 against the oracle."""
-    wl, env, sur = trained(torch)
+    wl, env, sur = trained_sur
     path = str(tmp_path / "sur.bin")
     sur.save(path)
     other = esp.Surrogate.load(env, path)
@@ -180,8 +180,8 @@ def test_failed_probe_makes_its_voxel_exact_in_the_same_call(torch, tmp_path):
         other.close()
 
 
-def test_save_load_round_trip(torch, tmp_path):
-    wl, env, sur = trained(torch)
+def test_save_load_round_trip(torch, trained_sur, tmp_path):
+    wl, env, sur = trained_sur
     path = str(tmp_path / "sur.bin")
     sur.save(path)
     other = esp.Surrogate.load(env, path)
