@@ -407,6 +407,7 @@ def surrogate_leg(args, env, wl, label, torch, stream, flush, exact_ms, V_exact=
            "near_entries": info["n_near_entries"], "far_entries": info["n_far_entries"],
            "near_share": info["n_near_entries"] / max(1, info["n_near_entries"] + info["n_far_entries"]),
            "train_s": t_train, "trusted_voxel_fraction": info["trusted_fraction"],
+           "expansion_only_trusted_voxel_fraction": info["baseline_trusted_fraction"],
            "far_valid_rms_err_ha": info["valid_rms_err"], "far_valid_max_err_ha": info["valid_max_err"],
            "expansion_only_rms_err_ha": info["baseline_rms_err"],
            "expansion_only_max_err_ha": info["baseline_max_err"], "expansion_coefficients": info["n_baseline"],

@@ -275,10 +275,10 @@ typedef struct esp_surrogate esp_surrogate;
 typedef struct {
     int32_t size;              /* sizeof(esp_surrogate_cfg), set by esp_surrogate_default_cfg */
     int32_t n_train;           /* training positions (2^19) */
-    int32_t n_valid;           /* validation positions for the trust map (2^17) */
+    int32_t n_valid;           /* validation positions for the trust map (2^17), plus one in every voxel */
     int32_t epochs;            /* passes over the training set (8) */
     int32_t batch;             /* mini-batch (8192) */
-    int32_t degree;            /* degree L of the far field's interior expansion (16; <= 40) */
+    int32_t degree;            /* degree L of the far field's interior expansion (12; <= 40) */
     double qm_radius;          /* radius of the QM sphere, bohr (6) */
     double position_sd;        /* sd of the walker law for half the samples (2) */
     double fourier_sigma;      /* sd of the Fourier frequencies, per unit radius (1) */
@@ -308,6 +308,7 @@ typedef struct {
     double baseline_rms_err;
     int64_t n_near_entries;    /* distributions + point charges summed exactly on every call */
     int64_t n_far_entries;     /* distributions + point charges replaced by expansion + network */
+    double baseline_trusted_fraction; /* share of voxels the expansion alone (no network) would earn */
 } esp_surrogate_stats;
 
 void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg);
@@ -346,6 +347,13 @@ esp_status esp_surrogate_features(const esp_surrogate *s, float *freq_out, doubl
  * coef_out (esp_harmonics order).  Adding an offset plants a known error in
  * every surrogate value, which the probe must catch. */
 esp_status esp_surrogate_debug_expansion(esp_surrogate *s, double dc, double *coef_out, int32_t max_coef);
+/* Iterations of each bounded wait (mbarrier) of the network's tensor-core
+ * kernel before it gives up: the kernel then records an error, waits (with the
+ * default limit) for its own copies and MMAs in flight, frees its tensor
+ * memory and returns, and the call returns ESP_ERR_TIMEOUT with the context
+ * still usable.  limit < 0 restores the default (about one second); 0 makes
+ * every first wait give up at once (used by the tests of that error path). */
+esp_status esp_surrogate_set_wait_limit(esp_surrogate *s, int32_t limit);
 /* Test hook: the network outputs y [n] (FP32 normalised residual, before the
  * baseline and scale are applied) of the fused tensor-core inference kernel
  * (tcgen05) at host positions [n][3], n <= 65536.  ESP_ERR_TIMEOUT if one of
@@ -389,6 +397,16 @@ int32_t esp_abi_version(void);
  * host (nmax <= ESP_MAX_L).  Lets CPU tests check the tables and the Taylor
  * and asymptotic branches without a GPU. */
 esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_out);
+
+/* Test hook: 1 if the host-side fault injection names `what` ("alloc",
+ * "upload" or "graph").  The environment variable ESP_FAULT (comma-separated
+ * names, read on every use) makes the named operations fail as if their CUDA
+ * call had failed: "alloc" every device allocation of the library (the call
+ * returns ESP_ERR_OOM), "upload" the environment upload of esp_create
+ * (ESP_ERR_CUDA), "graph" the instantiation of the batched driver's CUDA graph
+ * (ESP_ERR_CUDA).  Clearing the variable lets the next call succeed; no GPU
+ * fault is involved. */
+int32_t esp_debug_fault_active(const char *what);
 
 /* Test hook, not part of the evaluation path: the real regular solid
  * harmonics S_k(u), k < (L + 1)^2 (L <= 40), that the surrogate's far-field

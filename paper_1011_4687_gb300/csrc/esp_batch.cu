@@ -109,7 +109,7 @@ esp_status capture_graph(esp_batch *b)
     }
     if (e != cudaSuccess)
         return cuda_fail(e, "ending graph capture");
-    e = cudaGraphInstantiate(&b->exec, g, 0);
+    e = fault("graph") ? cudaErrorInvalidValue : cudaGraphInstantiate(&b->exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess)
         return cuda_fail(e, "instantiating the batched graph");

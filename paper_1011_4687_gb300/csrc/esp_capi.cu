@@ -515,9 +515,9 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const 
                         c->ppt[p], p == 0 ? "FP64" : "FP32C");
         }
     }
-    cudaError_t e;
+    cudaError_t e = fault("upload") ? cudaErrorInvalidValue : cudaSuccess;
     int64_t bytes = 0;
-    if ((e = upload(c->tiles, c->env.tiles, bytes)) != cudaSuccess ||
+    if (e != cudaSuccess || (e = upload(c->tiles, c->env.tiles, bytes)) != cudaSuccess ||
         (e = upload(c->rec32, c->env.rec32, bytes)) != cudaSuccess ||
         (e = upload(c->rec64, c->env.rec64, bytes)) != cudaSuccess ||
         (e = upload(c->boys32, boys_table32(), bytes)) != cudaSuccess ||
@@ -711,6 +711,8 @@ esp_status esp_debug_boys(int32_t precision, int32_t nmax, double T, double *F_o
     }
     return fail(ESP_ERR_INVALID, "unknown precision");
 }
+
+int32_t esp_debug_fault_active(const char *what) { return what && fault(what) ? 1 : 0; }
 
 esp_status esp_debug_solid_harmonics(int32_t L, const double *u, double *out)
 {

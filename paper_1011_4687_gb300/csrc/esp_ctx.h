@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -37,6 +38,30 @@ inline esp_status cuda_fail(cudaError_t e, const char *what)
     return fail(ESP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Host-side fault injection for the tests of the error paths (no GPU fault
+// is involved): the environment variable ESP_FAULT names, comma-separated, the
+// operations that fail as if the CUDA call had failed: "alloc" (every device
+// allocation of contexts, scratch, batches and surrogates: out of memory),
+// "upload" (the environment upload of esp_create), "graph" (instantiating the
+// batched driver's CUDA graph).  Read on every use, so a test can set and
+// clear it between calls.
+inline bool fault(const char *what)
+{
+    const char *v = std::getenv("ESP_FAULT");
+    if (!v || !*v)
+        return false;
+    const size_t n = std::strlen(what);
+    for (const char *p = v; *p;) {
+        const char *q = p;
+        while (*q && *q != ',')
+            ++q;
+        if (size_t(q - p) == n && std::strncmp(p, what, n) == 0)
+            return true;
+        p = *q ? q + 1 : q;
+    }
+    return false;
+}
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -51,6 +76,8 @@ struct DevBuf {
     {
         if (need <= bytes)
             return cudaSuccess;
+        if (fault("alloc"))
+            return cudaErrorMemoryAllocation;
         release();
         cudaError_t e = cudaMalloc(&p, need);
         if (e != cudaSuccess) {

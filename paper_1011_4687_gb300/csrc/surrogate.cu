@@ -83,6 +83,7 @@ struct esp_surrogate {
     int dim = 0;
     double train_loss = 0.0, valid_max_err = 0.0, trusted_fraction = 0.0;
     double valid_rms_err = 0.0, base_max_err = 0.0, base_rms_err = 0.0; // with the network / expansion alone
+    double base_trusted_fraction = 0.0; // the trust map of the expansion alone
     int64_t n_near_entries = 0, n_far_entries = 0;
     int probe_offset = 0;
     // near / far split of the context's tiles
@@ -95,6 +96,7 @@ struct esp_surrogate {
     DevBuf d_flag, d_pre, d_tot, d_count, d_cpos, d_cidx, d_cV, d_nfail;
     DevBuf d_wpk, d_tcerr, d_ynet;      // packed weights, kernel status, fused-inference outputs
     bool packed = false;                // d_wpk holds the current BF16 parameters
+    int wait_limit = tc_default_wait_limit(); // bounded waits of the network kernel
     int ynet_cap = 0;
     int chunk_cap = 0, fb_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
@@ -450,7 +452,8 @@ esp_status net_forward(esp_surrogate *s, const double *pos, int n, cudaStream_t 
     if ((e = cudaMemsetAsync(s->d_tcerr.p, 0, 4, st)) != cudaSuccess ||
         (e = tc_forward(pos, n, static_cast<const float *>(s->d_freq.p), s->centre, s->inv_r,
                         static_cast<const __nv_bfloat16 *>(s->d_wpk.p), static_cast<const float *>(s->d_params.p), lay,
-                        static_cast<float *>(s->d_ynet.p), static_cast<int *>(s->d_tcerr.p), st)) != cudaSuccess)
+                        static_cast<float *>(s->d_ynet.p), static_cast<int *>(s->d_tcerr.p), s->wait_limit, st)) !=
+        cudaSuccess)
         return cuda_fail(e, "surrogate network (tensor cores)");
     return ESP_OK;
 }
@@ -611,6 +614,26 @@ esp_status build_trust(esp_surrogate *s, const std::vector<double> &pos, const s
     return ESP_OK;
 }
 
+// One uniformly placed point in every trust-map voxel whose centre lies inside
+// the QM sphere, appended to pos (so that no voxel inside goes untrusted for
+// lack of validation points).
+void voxel_points(const esp_surrogate *s, std::mt19937_64 &rng, std::vector<double> &pos)
+{
+    const double vox = s->cfg.voxel, R = 1.0 / s->inv_r;
+    const int dim = int(std::ceil(2.0 * R / vox));
+    const double h = 0.5 * dim * vox;
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    for (int ix = 0; ix < dim; ++ix)
+        for (int iy = 0; iy < dim; ++iy)
+            for (int iz = 0; iz < dim; ++iz) {
+                const double c[3] = {-h + (ix + 0.5) * vox, -h + (iy + 0.5) * vox, -h + (iz + 0.5) * vox};
+                if (c[0] * c[0] + c[1] * c[1] + c[2] * c[2] >= R * R)
+                    continue;
+                for (int d = 0; d < 3; ++d)
+                    pos.push_back(s->centre[d] + c[d] + (U(rng) - 0.5) * vox);
+            }
+}
+
 esp_status download(std::vector<double> &out, const DevBuf &b, size_t n, cudaStream_t st)
 {
     out.resize(n);
@@ -660,17 +683,19 @@ esp_status train(esp_surrogate *s)
     std::vector<double> tpos, vpos;
     sample_positions(rng, cfg.n_train, s->centre, 1.0 / s->inv_r, cfg.position_sd, tpos);
     sample_positions(rng, cfg.n_valid, s->centre, 1.0 / s->inv_r, cfg.position_sd, vpos);
+    voxel_points(s, rng, vpos); // every voxel inside the sphere gets validation evidence
+    const int n_val = int(vpos.size() / 3);
     DevBuf d_tpos, d_tV, d_tE, d_vpos, d_vV, d_vS;
     if ((e = upload_vec(d_tpos, tpos)) != cudaSuccess || (e = upload_vec(d_vpos, vpos)) != cudaSuccess ||
         (e = d_tV.ensure(size_t(cfg.n_train) * 8)) != cudaSuccess ||
         (e = d_tE.ensure(size_t(cfg.n_train) * 8)) != cudaSuccess ||
-        (e = d_vV.ensure(size_t(cfg.n_valid) * 8)) != cudaSuccess ||
-        (e = d_vS.ensure(size_t(cfg.n_valid) * 8)) != cudaSuccess)
+        (e = d_vV.ensure(size_t(n_val) * 8)) != cudaSuccess ||
+        (e = d_vS.ensure(size_t(n_val) * 8)) != cudaSuccess)
         return cuda_fail(e, "allocating surrogate training data");
     const int lp = cfg.label_precision == ESP_FP64 ? 0 : 1;
     const double *tp = static_cast<const double *>(d_tpos.p), *vp = static_cast<const double *>(d_vpos.p);
     if ((r = far_exact(s, tp, cfg.n_train, static_cast<double *>(d_tV.p), lp)) != ESP_OK ||
-        (r = far_exact(s, vp, cfg.n_valid, static_cast<double *>(d_vV.p), lp)) != ESP_OK)
+        (r = far_exact(s, vp, n_val, static_cast<double *>(d_vV.p), lp)) != ESP_OK)
         return r;
     if ((e = expansion(tp, cfg.n_train, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p), s->degree,
                        nullptr, 0.0, false, static_cast<double *>(d_tE.p), st)) != cudaSuccess)
@@ -732,31 +757,36 @@ esp_status train(esp_surrogate *s)
         return cuda_fail(e, "reading trained weights");
     // validation of the far approximation against the exact far-tile sum, the
     // expansion alone as the method without the network, and the trust map
-    if ((r = far_approx(s, vp, cfg.n_valid, static_cast<double *>(d_vS.p), false, st)) != ESP_OK)
+    if ((r = far_approx(s, vp, n_val, static_cast<double *>(d_vS.p), false, st)) != ESP_OK)
         return r;
     std::vector<double> vS, vV, vE;
-    if ((r = download(vS, d_vS, size_t(cfg.n_valid), st)) != ESP_OK || (r = net_status(s)) != ESP_OK ||
-        (r = download(vV, d_vV, size_t(cfg.n_valid), st)) != ESP_OK)
+    if ((r = download(vS, d_vS, size_t(n_val), st)) != ESP_OK || (r = net_status(s)) != ESP_OK ||
+        (r = download(vV, d_vV, size_t(n_val), st)) != ESP_OK)
         return r;
-    if ((e = expansion(vp, cfg.n_valid, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p), s->degree,
+    if ((e = expansion(vp, n_val, s->centre, s->inv_r, static_cast<const double *>(s->d_coef.p), s->degree,
                        nullptr, 0.0, false, static_cast<double *>(d_vS.p), st)) != cudaSuccess)
         return cuda_fail(e, "expansion at the validation positions");
-    if ((r = download(vE, d_vS, size_t(cfg.n_valid), st)) != ESP_OK)
+    if ((r = download(vE, d_vS, size_t(n_val), st)) != ESP_OK)
         return r;
-    std::vector<double> err(cfg.n_valid);
+    std::vector<double> err(n_val), berr(n_val);
     double mx = 0.0, sq = 0.0, bmx = 0.0, bsq = 0.0;
-    for (int i = 0; i < cfg.n_valid; ++i) {
+    for (int i = 0; i < n_val; ++i) {
         err[size_t(i)] = std::fabs(vS[size_t(i)] - vV[size_t(i)]);
         mx = std::max(mx, err[size_t(i)]);
         sq += err[size_t(i)] * err[size_t(i)];
-        const double be = std::fabs(vE[size_t(i)] - vV[size_t(i)]);
-        bmx = std::max(bmx, be);
-        bsq += be * be;
+        berr[size_t(i)] = std::fabs(vE[size_t(i)] - vV[size_t(i)]);
+        bmx = std::max(bmx, berr[size_t(i)]);
+        bsq += berr[size_t(i)] * berr[size_t(i)];
     }
     s->valid_max_err = mx;
-    s->valid_rms_err = std::sqrt(sq / std::max(cfg.n_valid, 1));
+    s->valid_rms_err = std::sqrt(sq / std::max(n_val, 1));
     s->base_max_err = bmx;
-    s->base_rms_err = std::sqrt(bsq / std::max(cfg.n_valid, 1));
+    s->base_rms_err = std::sqrt(bsq / std::max(n_val, 1));
+    // the trust map the expansion alone would earn (the method without the
+    // network), then the surrogate's own
+    if ((r = build_trust(s, vpos, berr)) != ESP_OK)
+        return r;
+    s->base_trusted_fraction = s->trusted_fraction;
     if ((r = build_trust(s, vpos, err)) != ESP_OK)
         return r;
     if ((e = upload_vec(s->d_trust, s->trust)) != cudaSuccess)
@@ -894,7 +924,7 @@ void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg)
     cfg->n_valid = 1 << 17;
     cfg->epochs = 8;
     cfg->batch = 8192;
-    cfg->degree = 16;
+    cfg->degree = 12;
     cfg->qm_radius = 6.0;
     cfg->position_sd = 2.0;
     cfg->fourier_sigma = 1.0;
@@ -1013,6 +1043,7 @@ esp_status esp_surrogate_info(const esp_surrogate *s, esp_surrogate_stats *stats
     stats->baseline_rms_err = s->base_rms_err;
     stats->n_near_entries = s->n_near_entries;
     stats->n_far_entries = s->n_far_entries;
+    stats->baseline_trusted_fraction = s->base_trusted_fraction;
     return ESP_OK;
 }
 
@@ -1087,6 +1118,14 @@ esp_status esp_surrogate_debug_expansion(esp_surrogate *s, double dc, double *co
     return ESP_OK;
 }
 
+esp_status esp_surrogate_set_wait_limit(esp_surrogate *s, int32_t limit)
+{
+    if (!valid_sur(s))
+        return fail(ESP_ERR_INVALID, "invalid surrogate");
+    s->wait_limit = limit < 0 ? tc_default_wait_limit() : limit;
+    return ESP_OK;
+}
+
 esp_status esp_surrogate_features(const esp_surrogate *s, float *freq_out, double *centre_inv_r_out)
 {
     if (!valid_sur(s) || !freq_out || !centre_inv_r_out)
@@ -1113,7 +1152,8 @@ esp_status esp_surrogate_save(const esp_surrogate *s, const char *path)
     int32_t hdr[8] = {int32_t(kFileMagic), int32_t(kFileVersion), s->degree, s->ncoef, s->dim, int32_t(layout().total),
                       kFreq, 0};
     double dd[12] = {s->centre[0], s->centre[1], s->centre[2], s->inv_r, s->scale, s->train_loss, s->valid_max_err,
-                     s->trusted_fraction, s->valid_rms_err, s->base_max_err, s->base_rms_err, 0.0};
+                     s->trusted_fraction, s->valid_rms_err, s->base_max_err, s->base_rms_err,
+                     s->base_trusted_fraction};
     bool ok = put(hdr, sizeof(hdr)) && put(dd, sizeof(dd)) && put(&s->cfg, sizeof(s->cfg)) &&
               put(s->coef.data(), s->coef.size() * 8) && put(s->freq.data(), s->freq.size() * 4) &&
               put(s->params.data(), s->params.size() * 4) && put(s->trust.data(), s->trust.size());
@@ -1176,6 +1216,7 @@ esp_status esp_surrogate_load(esp_ctx *ctx, const char *path, esp_surrogate **ou
     s->valid_rms_err = dd[8];
     s->base_max_err = dd[9];
     s->base_rms_err = dd[10];
+    s->base_trusted_fraction = dd[11];
     s->ctx = ctx;
     // the near / far split is a function of the context's tiles and the configuration
     split_tiles(s);

@@ -43,9 +43,13 @@ size_t tc_packed_elems();
 cudaError_t tc_pack(const __nv_bfloat16 *wb, const TcLayout &lay, __nv_bfloat16 *wpk, cudaStream_t s);
 // y[i] = network output at position i (features, 4 hidden layers, output
 // layer); *err is set to 1 if a bounded wait of the kernel gave up.
+// wait_limit: iterations of each of the kernel's mbarrier waits before it
+// gives up (sets *err, drains its own copies, frees its tensor memory and
+// returns); tc_default_wait_limit() is about one second.
+int tc_default_wait_limit();
 cudaError_t tc_forward(const double *pos, int n, const float *freq, const double c[3], double inv_r,
                        const __nv_bfloat16 *wpk, const float *params, const TcLayout &lay, float *y, int *err,
-                       cudaStream_t s);
+                       int wait_limit, cudaStream_t s);
 cudaError_t features(const double *pos, int n, const float *freq, const double c[3], double inv_r,
                      __nv_bfloat16 *X, cudaStream_t s);
 // y[i] = H[i] . w + *b; with targets t: dy = 2 (y - t) / n and squared errors

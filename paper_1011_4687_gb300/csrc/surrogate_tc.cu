@@ -43,7 +43,11 @@ constexpr int kChunkBytes = kHidden * kChunkK * 2; // 32 KB
 constexpr int kABytes = kRows * kHidden * 2;     // 64 KB activation operand
 constexpr int kWBytes = kHidden * kHidden * 2;   // 128 KB: one whole layer of weights
 constexpr int kTmemCols = 256;                   // FP32 accumulator columns (N)
-// bounded waits: ~1 s at a few hundred ns per suspended try_wait
+// Bounded waits.  The main waits take their limit from the caller
+// (tc_default_wait_limit(): ~1 s at a few hundred ns per suspended try_wait);
+// after a wait has given up, the clean-up waits for this CTA's own copies and
+// MMAs in flight always use the default, so no asynchronous write into shared
+// or tensor memory outlives the CTA's allocations.
 constexpr int kWaitLimit = 1 << 22;
 
 // Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5),
@@ -74,9 +78,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit)
 {
-    for (int it = 0; it < kWaitLimit; ++it) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -156,7 +160,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_tc_kernel(const double *__restrict__ pos, int n, const float *__restrict__ freq, double cx, double cy,
                   double cz, double inv_r, const __nv_bfloat16 *__restrict__ wpk, const float *__restrict__ params,
-                  TcLayout lay, float *__restrict__ y, int *__restrict__ err, int n_tiles)
+                  TcLayout lay, float *__restrict__ y, int *__restrict__ err, int n_tiles, int wait_limit)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem;
@@ -204,6 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     uint32_t wpar[kHidden / kChunkK] = {0, 0, 0, 0};
     uint32_t mpar = 0;
+    bool mma_pending = false;   // a commit whose completion nobody has seen (after a failed wait)
+    uint32_t mma_pending_par = 0;
     const int q = warp & 3, hcol = (warp >> 2) * kGroupCols;
     const int row = q * 32 + lane;
     bool ok = true;
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (tid == 0) {
                 tc_fence_after();
                 for (int c = 0; c < nchunk; ++c) {
-                    if (!(wok = mbar_wait(smem_u32(&bar_w[c]), wpar[c])))
+                    if (!(wok = mbar_wait(smem_u32(&bar_w[c]), wpar[c], wait_limit)))
                         break;
 #pragma unroll
                     for (int ks = 0; ks < kChunkK; ks += 16) {
@@ -265,7 +271,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             for (int c = 0; c < nchunk; ++c)
                 wpar[c] ^= 1u;
-            const bool mok = mbar_wait(smem_u32(&bar_mma), mpar);
+            const bool mok = mbar_wait(smem_u32(&bar_mma), mpar, wait_limit);
+            if (!mok) {
+                mma_pending = true;
+                mma_pending_par = mpar;
+            }
             mpar ^= 1u;
             tc_fence_after();
             if (__syncthreads_or((wok && mok) ? 0 : 1)) {
@@ -325,9 +335,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!ok && tid == 0) {
         atomicExch(err, 1);
         // let weight copies still in flight land before the CTA's shared
-        // memory is released (a completed or unused chunk returns at once)
+        // memory is released (a completed or unused chunk returns at once),
+        // and the MMAs of a commit nobody waited for finish before the tensor
+        // memory is freed
         for (int c = 0; c < kHidden / kChunkK; ++c)
-            mbar_wait(smem_u32(&bar_w[c]), wpar[c] ^ 1u);
+            mbar_wait(smem_u32(&bar_w[c]), wpar[c] ^ 1u, kWaitLimit);
+        if (mma_pending)
+            mbar_wait(smem_u32(&bar_mma), mma_pending_par, kWaitLimit);
     }
     tc_fence_before();
     __syncthreads();
@@ -364,9 +378,11 @@ cudaError_t tc_pack(const __nv_bfloat16 *wb, const TcLayout &lay, __nv_bfloat16 
     return cudaGetLastError();
 }
 
+int tc_default_wait_limit() { return kWaitLimit; }
+
 cudaError_t tc_forward(const double *pos, int n, const float *freq, const double c[3], double inv_r,
                        const __nv_bfloat16 *wpk, const float *params, const TcLayout &lay, float *y, int *err,
-                       cudaStream_t s)
+                       int wait_limit, cudaStream_t s)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -381,7 +397,7 @@ cudaError_t tc_forward(const double *pos, int n, const float *freq, const double
     const int n_tiles = (n + kRows - 1) / kRows;
     const int grid = n_tiles < sms ? n_tiles : sms; // one persistent CTA per SM
     mlp_tc_kernel<<<grid, kThreads, smem, s>>>(pos, n, freq, c[0], c[1], c[2], inv_r, wpk, params, lay, y, err,
-                                               n_tiles);
+                                               n_tiles, wait_limit < 0 ? 0 : wait_limit);
     return cudaGetLastError();
 }
 

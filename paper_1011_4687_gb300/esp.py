@@ -87,7 +87,7 @@ class SurrogateStats(ctypes.Structure):
                 ("trusted_fraction", ctypes.c_double), ("n_params", ctypes.c_int64), ("n_baseline", ctypes.c_int64),
                 ("valid_rms_err", ctypes.c_double), ("baseline_max_err", ctypes.c_double),
                 ("baseline_rms_err", ctypes.c_double), ("n_near_entries", ctypes.c_int64),
-                ("n_far_entries", ctypes.c_int64)]
+                ("n_far_entries", ctypes.c_int64), ("baseline_trusted_fraction", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -185,8 +185,12 @@ def load(build_if_missing: bool = False):
     lib.esp_surrogate_debug_step.restype = ctypes.c_int
     lib.esp_surrogate_features.argtypes = [P, P, P]
     lib.esp_surrogate_features.restype = ctypes.c_int
+    lib.esp_surrogate_set_wait_limit.argtypes = [P, i32]
+    lib.esp_surrogate_set_wait_limit.restype = ctypes.c_int
     lib.esp_surrogate_debug_expansion.argtypes = [P, d, P, i32]
     lib.esp_surrogate_debug_expansion.restype = ctypes.c_int
+    lib.esp_debug_fault_active.argtypes = [ctypes.c_char_p]
+    lib.esp_debug_fault_active.restype = i32
     lib.esp_debug_solid_harmonics.argtypes = [i32, P, P]
     lib.esp_debug_solid_harmonics.restype = ctypes.c_int
     lib.esp_surrogate_debug_net.argtypes = [P, P, i32, P]
@@ -386,6 +390,11 @@ def measure_peaks(device: int = -1) -> dict:
     return p.as_dict()
 
 
+def debug_fault_active(what: str) -> bool:
+    """Test hook: does the host-side fault injection (ESP_FAULT) name `what`?"""
+    return bool(load().esp_debug_fault_active(what.encode()))
+
+
 def debug_solid_harmonics(L: int, u) -> np.ndarray:
     """Test hook: the surrogate's real regular solid harmonics S_k(u), k < (L+1)^2, on the host."""
     u = np.ascontiguousarray(u, np.float64).reshape(3)
@@ -569,6 +578,10 @@ class Surrogate:
         y = np.zeros(pos.shape[0], np.float32)
         _check(load().esp_surrogate_debug_net(self._s, pos.ctypes.data, pos.shape[0], y.ctypes.data))
         return y
+
+    def set_wait_limit(self, limit: int = -1):
+        """Iterations of the network kernel's bounded waits (-1: the default)."""
+        _check(load().esp_surrogate_set_wait_limit(self._s, int(limit)))
 
     def debug_expansion(self, dc: float = 0.0) -> np.ndarray:
         """Test hook: add dc to the expansion's constant coefficient; returns the coefficients."""

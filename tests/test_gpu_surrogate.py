@@ -149,11 +149,27 @@ def test_served_positions_match_oracle(torch, trained_sur):
 
 def test_network_gains_over_expansion_alone(trained_sur):
     """The method without the network (the far field's expansion alone) against
-    the same with the network, on the validation set of the far field."""
+    the same with the network, on the validation set of the far field: at the
+    default degree the network lowers the error and serves at least as many
+    voxels."""
     wl, env, sur = trained_sur
     info = sur.info()
     assert info["valid_rms_err"] < info["baseline_rms_err"], info
-    assert info["valid_max_err"] <= TOL / 2 or info["trusted_fraction"] < 1.0
+    assert info["valid_max_err"] < info["baseline_max_err"], info
+    assert info["trusted_fraction"] >= info["baseline_trusted_fraction"], info
+
+
+def test_network_gain_at_low_expansion_degree(torch):
+    """With a degree-8 expansion the far field's truncation error is well above
+    the tolerance; the trained network removes most of it (rms at least 4x
+    lower) and earns many more trusted voxels than the expansion alone."""
+    wl = realistic()
+    with esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs) as env:
+        with esp.Surrogate(env, n_train=1 << 18, n_valid=1 << 16, epochs=8, degree=8) as sur:
+            info = sur.info()
+    assert info["baseline_max_err"] > TOL, info
+    assert info["valid_rms_err"] * 4 <= info["baseline_rms_err"], info
+    assert info["trusted_fraction"] >= info["baseline_trusted_fraction"] + 0.2, info
 
 
 def test_failed_probe_makes_its_voxel_exact_in_the_same_call(torch, trained_sur, tmp_path):
