@@ -463,18 +463,23 @@ def esp_mod():
     return esp
 
 
-def latency_leg(args, esp, torch, stream):
+def latency_leg(args, esp, torch, stream, oracle_mod=None):
     """The paper's own call pattern: its cell count (268,782 point cells +
-    36 nuclei) evaluated at one position per call (one Metropolis move), and at
-    16 per call; microseconds per call on the device (CUDA events, device
-    buffers) and through host buffers (wall clock, copies included)."""
+    36 nuclei) evaluated at 1, 16 and 128 positions per call (one Metropolis
+    move is one position): microseconds per call on the device (CUDA events,
+    device buffers), replayed as a captured graph, and through host buffers
+    (wall clock, copies included).  Cells are summed in compensated FP32,
+    nuclei in FP64."""
     from workloads import point_cells_environment
-    wl = point_cells_environment(seed=1011 * 100 + 6, n_cells=268782, n_nuclei=36, n_positions=16)
+    wl = point_cells_environment(seed=1011 * 100 + 6, n_cells=268782, n_nuclei=36, n_positions=128)
     env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c", stream=stream.cuda_stream)
     units = env.info()["n_point_charges"]
-    out = {"workload": "%d point charges (268,782 cells + 36 nuclei)" % units}
+    out = {"workload": "%d point charges (268,782 cells + 36 nuclei)" % units, "precision": "FP32C"}
     reps = 200
-    for npos in (1, 16):
+    ref = None
+    if oracle_mod is not None:
+        ref = oracle_mod.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    for npos in (1, 16, 128):
         pos = torch.from_numpy(wl.positions[:npos].copy()).cuda()
         V = torch.empty(npos, dtype=torch.float64, device="cuda")
         for _ in range(10):
@@ -488,14 +493,29 @@ def latency_leg(args, esp, torch, stream):
         s1.record(stream)
         s1.synchronize()
         us = s0.elapsed_time(s1) * 1e3 / reps
+        Vg = torch.empty(npos, dtype=torch.float64, device="cuda")
+        with esp.Graph(env, pos, Vg) as g:
+            for _ in range(10):
+                g.launch()
+            torch.cuda.synchronize()
+            s0.record(stream)
+            for _ in range(reps):
+                g.launch()
+            s1.record(stream)
+            s1.synchronize()
+            us_graph = s0.elapsed_time(s1) * 1e3 / reps
         hp = wl.positions[:npos].copy()
         hv = np.zeros(npos)
         t0 = time.perf_counter()
         for _ in range(reps):
             env.eval(hp, out=hv)
         us_host = (time.perf_counter() - t0) * 1e6 / reps
-        out["positions_%d" % npos] = {"us_per_call": us, "us_per_call_host_buffers": us_host,
-                                      "evals_per_s": units * npos / (us * 1e-6), "launches_per_call": 2}
+        leg = {"us_per_call": us, "us_per_call_graph_replay": us_graph, "us_per_call_host_buffers": us_host,
+               "evals_per_s": units * npos / (us * 1e-6), "launches_per_call": 2}
+        if ref is not None:
+            leg["max_point_err_ha"] = float(np.abs(Vg.cpu().numpy() - ref[:npos]).max())
+        out["positions_%d" % npos] = leg
+    out["ratio_16_vs_1"] = out["positions_16"]["us_per_call"] / out["positions_1"]["us_per_call"]
     env.close()
     return out
 
@@ -818,7 +838,7 @@ def main(argv=None):
         out["batch"] = batch_leg(args, esp, torch, stream, flush, batch_wls, oracle_mod)
         del batch_wls
     if not args.no_latency:
-        out["few_positions_per_call"] = latency_leg(args, esp, torch, stream)
+        out["few_positions_per_call"] = latency_leg(args, esp, torch, stream, oracle_mod)
     if not args.no_surrogate:
         sur_legs["small"] = small_surrogate_leg(args, torch, stream, flush, oracle_mod)
         out["surrogate"] = sur_legs

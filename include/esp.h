@@ -115,6 +115,10 @@ typedef struct {
                                       FP64, for tiles holding a distribution whose potential
                                       can exceed 2 Ha (a compact charge not merged into a
                                       point charge); < 0 = default (1.5 bohr), 0 = off */
+    double point32_max_charge;     /* FP32C: point charges with |Z| at or below this (the paper's
+                                      density cells) are summed in compensated FP32 like the
+                                      distributions, larger ones (nuclei, merged monopoles) in
+                                      FP64; < 0 = default (0.25), 0 = every point charge FP64 */
 } esp_options;
 
 /* Per-context facts, for reporting and for counting evaluations. */
@@ -199,6 +203,35 @@ esp_status esp_eval_walkers(esp_ctx *ctx, const double *positions, int64_t n_wal
  * Errors: ESP_ERR_INVALID (n > ESP_NOALLOC_MAX_POSITIONS, host pointers, null
  * pointers), ESP_ERR_STATE, ESP_ERR_CUDA.  Calls no cudaMalloc or cudaFree. */
 esp_status esp_eval_noalloc(esp_ctx *ctx, const double *positions, int64_t n, double *V_out);
+
+/* ------------------------------------------------------------------------
+ * The paper's call pattern as a replayed CUDA graph.  The paper evaluates one
+ * electron position per call, once per Metropolis move (Sec. III,
+ * Fig. codeStructure: r_new in, U_ES out).  esp_graph_create captures the
+ * few-position evaluation of a fixed device position buffer into a fixed
+ * device output once; each esp_graph_launch replays it on the context's
+ * stream, so the caller writes the next positions into the same buffer (on
+ * that stream, or before the launch) and reads V after it.  The precision is
+ * the context's at creation (ESP_FP32C: small point charges in compensated
+ * FP32, everything else FP64; ESP_FP64: all FP64).
+ * ------------------------------------------------------------------------ */
+#define ESP_GRAPH_MAX_POSITIONS 128
+typedef struct esp_graph esp_graph;
+
+/* positions [n][3] and V_out [n] float64, device memory of the context's
+ * device, 1 <= n <= ESP_GRAPH_MAX_POSITIONS; both must stay allocated while
+ * the graph exists, and the context must outlive the graph.  The graph owns
+ * its scratch (partial sums).  Errors: ESP_ERR_INVALID, ESP_ERR_STATE,
+ * ESP_ERR_UNSUPPORTED (empty environment), ESP_ERR_OOM, ESP_ERR_CUDA. */
+esp_status esp_graph_create(esp_ctx *ctx, const double *positions, int64_t n, double *V_out, esp_graph **out);
+
+/* V_out = potentials at the buffer's current positions; enqueued on the
+ * context's stream, returns without waiting.  Errors: ESP_ERR_STATE,
+ * ESP_ERR_CUDA. */
+esp_status esp_graph_launch(esp_graph *g);
+
+/* Waits for the context's stream and frees the graph.  NULL is a no-op. */
+void esp_graph_destroy(esp_graph *g);
 
 /* ------------------------------------------------------------------------
  * Batched evaluation of many independent systems (environment, positions).
@@ -433,12 +466,13 @@ esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int6
  * context's environment, counted by the regime of its Boys argument
  * T = p |P - C|^2 (Sec. II.B, Eq. ElectrostaticField generalised to Hermite
  * Gaussian distributions; the regime decides which form of F_n(T) a term
- * needs and so its operation count).  counts (int64, 31 entries):
+ * needs and so its operation count).  counts (int64, 32 entries):
  *   counts[(L + 5 s) * 3 + b]  L = 0..4 total angular momentum, s = 1 for
  *                              distributions whose monopole sits in a point
  *                              charge (short-range remainder), b = 0: T < 30,
  *                              1: 30 <= T < 45, 2: T >= 45;
- *   counts[30]                 point-charge terms.
+ *   counts[30]                 point-charge terms summed in FP64;
+ *   counts[31]                 point-charge terms summed in FP32 (small charges).
  * Synchronous; allocates and frees a small device buffer.  Errors:
  * ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_CUDA, ESP_ERR_OOM. */
 esp_status esp_work_census(esp_ctx *ctx, const double *positions, int64_t n, int64_t *counts);

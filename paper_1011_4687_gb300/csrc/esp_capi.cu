@@ -91,8 +91,14 @@ void esp::set_tile_groups(const std::vector<TileMeta> &T, TileView &v)
     // FP32 operations per evaluation by L (the kernel's algorithmic count) and
     // an FP64 point charge, for the split of the work between groups
     static const double kCost[kMaxL + 1] = {10.0, 26.0, 52.0, 95.0, 170.0};
-    const double kPointCost = 12.0;
+    const double kPointCost = 12.0, kPoint32Cost = 10.0;
     v.n_tiles = int(T.size());
+    int64_t n_small = 0, n_all = 0;
+    for (const TileMeta &m : T) {
+        n_all += m.n;
+        n_small += m.cls == kClassPoint32 ? m.n : 0;
+    }
+    v.point_heavy = n_all > 0 && n_small * 10 >= n_all * 9;
     v.n_groups = 1;
     v.grp_tile[0] = 0;
     v.grp_tile[1] = int(T.size());
@@ -101,8 +107,8 @@ void esp::set_tile_groups(const std::vector<TileMeta> &T, TileView &v)
     int bounds[kMaxTileGroups + 1];
     double work[kMaxTileGroups] = {0.0};
     for (size_t t = 0; t < T.size(); ++t) {
-        const int g = T[t].cls == kClassPoint ? 0 : 1 + (T[t].cls & 7);
-        if (g < prev || g > kMaxL + 1)
+        const int g = T[t].cls == kClassPoint ? 0 : T[t].cls == kClassPoint32 ? 1 : 2 + (T[t].cls & 7);
+        if (g < prev || g > kMaxL + 2)
             return; // not grouped by class: keep the plain deal
         if (g != prev) {
             if (n == kMaxTileGroups)
@@ -110,7 +116,7 @@ void esp::set_tile_groups(const std::vector<TileMeta> &T, TileView &v)
             bounds[n++] = int(t);
             prev = g;
         }
-        work[n - 1] += T[t].n * (g == 0 ? kPointCost : kCost[g - 1]);
+        work[n - 1] += T[t].n * (g == 0 ? kPointCost : g == 1 ? kPoint32Cost : kCost[g - 2]);
     }
     if (n == 0)
         return;
@@ -162,8 +168,11 @@ Staged staged_view(esp_ctx *c, int64_t n)
 esp_status pipeline(esp_ctx *c, const TileView &v, int prec, const double *d_pos, int64_t n, double *dV,
                     int64_t n_walkers, int64_t n_elec, double *dE, bool timing)
 {
-    // few positions: entries spread over threads instead of positions
-    const bool small_n = n <= kSmallN && v.n_tiles > 0;
+    // few positions: entries spread over threads instead of positions (up to
+    // kSmallN positions for environments of point charges, whose entries the
+    // path evaluates in FP32; up to kSmallNDistributions otherwise, since
+    // distributions take FP64 there)
+    const bool small_n = v.n_tiles > 0 && (n <= kSmallNDistributions || (n <= kSmallN && v.point_heavy));
     EvalArgs a;
     const int splits = small_n ? small_n_splits(v.n_tiles, c->num_sms) : plan_splits(c, v, int(n), prec, 1 << 20, a);
     esp_status st = ensure_scratch(c, n, splits, false, n_walkers);
@@ -210,7 +219,10 @@ esp_status pipeline(esp_ctx *c, const TileView &v, int prec, const double *d_pos
         sa.cz = c->opt.qm_center[2];
         sa.tiles = v.tiles;
         sa.rec64 = a.rec64;
+        sa.rec32 = a.rec32;
         sa.boys64 = a.boys64;
+        sa.quantum = c->env.coord_quantum;
+        sa.fp32 = prec == 1;
         sa.partial = a.partial;
         if ((e = launch_small_n(sa, splits, dV, s)) != cudaSuccess)
             return cuda_fail(e, "launching the few-position kernels");
@@ -359,6 +371,11 @@ double host_eval_f32c(const esp_ctx *c, const double *C)
             tile_points_f64<1>(c->env.rec64.data() + m.off64, m.n, c64, acc64);
             continue;
         }
+        if (m.cls == kClassPoint32) {
+            const bool none[1] = {false};
+            tile_f32c<0, 1, true, false, false>(c->env.rec32.data() + m.off32, m.n, ch, cl, none, S, Cc, boys32);
+            continue;
+        }
         bool nearq[1], farq;
         classify_tile(m, ch[0][0], ch[0][1], ch[0][2], near_r, nearq[0], farq);
         const float *r = c->env.rec32.data() + m.off32;
@@ -396,7 +413,7 @@ double host_eval_f64(const esp_ctx *c, const double *C)
     for (const TileMeta &m : c->env.tiles) {
         const double *r = c->env.rec64.data() + m.off64;
         double v;
-        if (m.cls == kClassPoint) {
+        if (is_point_class(m.cls)) {
             double c64[1][3] = {{C[0], C[1], C[2]}}, acc[1] = {0.0};
             tile_points_f64<1>(r, m.n, c64, acc);
             v = acc[0];
@@ -423,6 +440,7 @@ void esp_default_options(esp_options *opt)
     opt->cuda_stream = nullptr;
     opt->device = -1;
     opt->near_radius = -1.0;
+    opt->point32_max_charge = -1.0;
 }
 
 int32_t esp_abi_version(void) { return ESP_ABI_VERSION; }
@@ -463,6 +481,8 @@ esp_status esp_create(const esp_point_charge *charges, int64_t n_charges, const 
         return fail(ESP_ERR_INVALID, "unknown flags 0x%x", opt.flags);
     if (!(opt.near_radius < 1e6))
         return fail(ESP_ERR_INVALID, "bad near_radius");
+    if (!(opt.point32_max_charge < 1e30))
+        return fail(ESP_ERR_INVALID, "bad point32_max_charge");
     const int thr_ok[] = {0, 64, 128, 256};
     bool tok = false;
     for (int t : thr_ok)

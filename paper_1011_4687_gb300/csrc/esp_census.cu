@@ -24,23 +24,23 @@ constexpr int kCensusThreads = 128;
 constexpr int kCensusMaxPositions = ESP_CENSUS_MAX_POSITIONS; // 48 KB of positions in shared memory
 
 // counts layout: [(L + 5 * short) * 3 + band] for band 0: T < 30, 1: 30 <= T < 45,
-// 2: T >= 45; [30]: point-charge terms
+// 2: T >= 45; [30]: FP64 point-charge terms; [31]: FP32 point-charge terms
 __global__ void __launch_bounds__(kCensusThreads) census_kernel(const TileMeta *__restrict__ tiles,
                                                                 const double *__restrict__ rec64,
                                                                 const float *__restrict__ pos, int n,
                                                                 unsigned long long *__restrict__ counts)
 {
     __shared__ float s_pos[kCensusMaxPositions * 3];
-    __shared__ unsigned long long s_cnt[31];
+    __shared__ unsigned long long s_cnt[32];
     for (int i = threadIdx.x; i < n * 3; i += kCensusThreads)
         s_pos[i] = pos[i];
-    if (threadIdx.x < 31)
+    if (threadIdx.x < 32)
         s_cnt[threadIdx.x] = 0ull;
     __syncthreads();
     const TileMeta m = tiles[blockIdx.x];
-    if (m.cls == kClassPoint) {
+    if (is_point_class(m.cls)) {
         if (threadIdx.x == 0)
-            atomicAdd(&s_cnt[30], (unsigned long long)m.n * (unsigned long long)n);
+            atomicAdd(&s_cnt[m.cls == kClassPoint ? 30 : 31], (unsigned long long)m.n * (unsigned long long)n);
     } else {
         const int L = m.cls & 7;
         const int base = (L + ((m.cls & kClassShortBit) ? 5 : 0)) * 3;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kCensusThreads) census_kernel(const TileMeta *
         }
     }
     __syncthreads();
-    if (threadIdx.x < 31 && s_cnt[threadIdx.x])
+    if (threadIdx.x < 32 && s_cnt[threadIdx.x])
         atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
@@ -92,19 +92,19 @@ extern "C" esp_status esp_work_census(esp_ctx *ctx, const double *positions, int
     unsigned long long *d_cnt = nullptr;
     cudaError_t e = cudaMalloc(&d_pos, std::max<size_t>(rel.size(), 1) * sizeof(float));
     if (e == cudaSuccess)
-        e = cudaMalloc(&d_cnt, 31 * sizeof(unsigned long long));
+        e = cudaMalloc(&d_cnt, 32 * sizeof(unsigned long long));
     cudaStream_t s = ctx->stream;
     if (e == cudaSuccess && n > 0)
         e = cudaMemcpyAsync(d_pos, rel.data(), rel.size() * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(d_cnt, 0, 31 * sizeof(unsigned long long), s);
+        e = cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), s);
     if (e == cudaSuccess && n > 0 && ctx->n_tiles > 0) {
         census_kernel<<<ctx->n_tiles, kCensusThreads, 0, s>>>(static_cast<const TileMeta *>(ctx->tiles.p),
                                                                static_cast<const double *>(ctx->rec64.p), d_pos,
                                                                int(n), d_cnt);
         e = cudaGetLastError();
     }
-    unsigned long long h[31] = {0};
+    unsigned long long h[32] = {0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
@@ -115,7 +115,7 @@ extern "C" esp_status esp_work_census(esp_ctx *ctx, const double *positions, int
         cudaFree(d_cnt);
     if (e != cudaSuccess)
         return cuda_fail(e, "work census");
-    for (int k = 0; k < 31; ++k)
+    for (int k = 0; k < 32; ++k)
         counts[k] = int64_t(h[k]);
     return ESP_OK;
 }

@@ -146,6 +146,7 @@ struct TileView {
     int n_groups = 1;
     int grp_tile[kMaxTileGroups + 1] = {0, 0};
     double grp_work[kMaxTileGroups] = {0.0};
+    bool point_heavy = false; // >= 90 % of the entries are FP32 point charges
 };
 
 // Tile groups of a host tile list (in device order); with fewer than one

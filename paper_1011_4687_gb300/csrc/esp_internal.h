@@ -27,7 +27,16 @@
 namespace esp {
 
 constexpr int kMaxL = 4;
-constexpr int kClassPoint = 5;          // tile class of point charges
+constexpr int kClassPoint = 5;          // tile class of point charges summed in FP64
+// Tile class of small point charges (|Z| <= point32_max_charge, the paper's
+// density cells) summed in compensated FP32: FP32 records in the L = 0 layout
+// (centre hi/lo, M_000 = Z with its low word) evaluated by the far form, and
+// FP64 records in the point layout [x, y, z, Z] for the FP64 paths.
+constexpr int kClassPoint32 = 6;
+constexpr double kDefaultPoint32Max = 0.25;
+ESP_HD constexpr bool is_point_class(int cls) { return cls == kClassPoint || cls == kClassPoint32; }
+// FP32 record stride of a tile class (point charges use the L = 0 layout)
+ESP_HD constexpr int rec32_stride_cls(int cls);
 // FP64 re-evaluation radius of the FP32C kernel when the caller leaves it unset.
 // It applies only to tiles holding a distribution whose potential can exceed
 // kNearVmax (|Q| 2 sqrt(p/pi) bounds the potential of a charge Q spread with
@@ -55,6 +64,7 @@ ESP_HD constexpr int rec32_pslo(int L) { return 9 + (L + 1) * (L + 2) * (L + 3) 
 ESP_HD constexpr int rec32_g(int L) { return 10 + (L + 1) * (L + 2) * (L + 3) / 6; }
 ESP_HD constexpr int rec32_stride(int L) { return ((10 + 2 * ((L + 1) * (L + 2) * (L + 3) / 6) + 3) / 4) * 4; }
 constexpr int kRec32MaxStride = 80;
+ESP_HD constexpr int rec32_stride_cls(int cls) { return cls == kClassPoint32 ? rec32_stride(0) : rec32_stride(cls & 7); }
 // FP64 record stride (doubles): [Px, Py, Pz, sqrt(p), G_0 .. G_{n-1}], padded to 2.
 ESP_HD constexpr int rec64_stride(int L) { return ((4 + (L == 0 ? 1 : L == 1 ? 4 : L == 2 ? 10 : L == 3 ? 20 : 35) + 1) / 2) * 2; }
 constexpr int kPointStride64 = 4;        // [x, y, z, Z]

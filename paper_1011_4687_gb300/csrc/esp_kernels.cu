@@ -257,52 +257,83 @@ constexpr int kSmallThreads = 64; // one thread per entry of a full tile
 __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
 {
     __shared__ double s_pos[kSmallN][3];
-    __shared__ double s_red[kSmallThreads / 32][kSmallN];
+    __shared__ float s_ph[kSmallN][3], s_pl[kSmallN][3]; // FP32 hi (on the records' grid) and lo words
+    __shared__ double s_red[kSmallThreads / 32][kSmallChunk];
     const int n = a.n_pos;
-    for (int i = threadIdx.x; i < n * 3; i += kSmallThreads)
-        s_pos[i / 3][i % 3] = a.pos_in[i] - (i % 3 == 0 ? a.cx : i % 3 == 1 ? a.cy : a.cz);
+    for (int i = threadIdx.x; i < n * 3; i += kSmallThreads) {
+        const double x = a.pos_in[i] - (i % 3 == 0 ? a.cx : i % 3 == 1 ? a.cy : a.cz);
+        const double h = nearbyint(x / a.quantum) * a.quantum;
+        s_pos[i / 3][i % 3] = x;
+        s_ph[i / 3][i % 3] = float(h);
+        s_pl[i / 3][i % 3] = float(x - h);
+    }
     __syncthreads();
-    double acc[kSmallN];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q0 = 0; q0 < n; q0 += kSmallChunk) {
+        const int nq = min(kSmallChunk, n - q0);
+        double acc[kSmallChunk];
 #pragma unroll
-    for (int q = 0; q < kSmallN; ++q)
-        acc[q] = 0.0;
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        const TileMeta m = a.tiles[t];
-        const bool pts = m.cls == kClassPoint;
-        const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
-        for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
-            const double *r = a.rec64 + m.off64 + (size_t)j * st;
+        for (int q = 0; q < kSmallChunk; ++q)
+            acc[q] = 0.0;
+        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+            const TileMeta m = a.tiles[t];
+            if (m.cls == kClassPoint32 && a.fp32) {
+                for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
+                    const float *r = a.rec32 + m.off32 + (size_t)j * rec32_stride(0);
+                    const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
+                    const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
+                    const float qh = r[rec32_m(0)], ql = r1.w;
 #pragma unroll
-            for (int q = 0; q < kSmallN; ++q) {
-                if (q >= n)
-                    break;
-                if (pts) {
-                    const double dx = r[0] - s_pos[q][0], dy = r[1] - s_pos[q][1], dz = r[2] - s_pos[q][2];
-                    acc[q] += r[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
-                } else {
-                    acc[q] += tile_f64_one_any(m.cls, r, 1, s_pos[q][0], s_pos[q][1], s_pos[q][2], a.boys64);
+                    for (int q = 0; q < kSmallChunk; ++q) {
+                        if (q >= nq)
+                            break;
+                        const int k = q0 + q;
+                        const float dx = (r0.x - s_ph[k][0]) + (r1.x - s_pl[k][0]);
+                        const float dy = (r0.y - s_ph[k][1]) + (r1.y - s_pl[k][1]);
+                        const float dz = (r0.z - s_ph[k][2]) + (r1.z - s_pl[k][2]);
+                        const float rs = esp_rsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                        acc[q] += double(fmaf(qh, rs, ql * rs));
+                    }
+                }
+                continue;
+            }
+            const bool pts = is_point_class(m.cls);
+            const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
+            for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
+                const double *r = a.rec64 + m.off64 + (size_t)j * st;
+#pragma unroll
+                for (int q = 0; q < kSmallChunk; ++q) {
+                    if (q >= nq)
+                        break;
+                    const int k = q0 + q;
+                    if (pts) {
+                        const double dx = r[0] - s_pos[k][0], dy = r[1] - s_pos[k][1], dz = r[2] - s_pos[k][2];
+                        acc[q] += r[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
+                    } else {
+                        acc[q] += tile_f64_one_any(m.cls, r, 1, s_pos[k][0], s_pos[k][1], s_pos[k][2], a.boys64);
+                    }
                 }
             }
         }
-    }
-    // fixed-order reduction per position: warp shuffles, then the warps in order
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        // fixed-order reduction per position: warp shuffles, then the warps in order
 #pragma unroll
-    for (int q = 0; q < kSmallN; ++q) {
-        if (q >= n)
-            break;
-        double v = acc[q];
-        for (int o = 16; o; o >>= 1)
-            v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0)
-            s_red[warp][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < n) {
-        double v = 0.0;
-        for (int w = 0; w < kSmallThreads / 32; ++w)
-            v += s_red[w][threadIdx.x];
-        a.partial[(size_t)blockIdx.x * n + threadIdx.x] = v;
+        for (int q = 0; q < kSmallChunk; ++q) {
+            if (q >= nq)
+                break;
+            double v = acc[q];
+            for (int o = 16; o; o >>= 1)
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                s_red[warp][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nq) {
+            double v = 0.0;
+            for (int w = 0; w < kSmallThreads / 32; ++w)
+                v += s_red[w][threadIdx.x];
+            a.partial[(size_t)blockIdx.x * n + q0 + threadIdx.x] = v;
+        }
+        __syncthreads(); // s_red is reused by the next chunk
     }
 }
 

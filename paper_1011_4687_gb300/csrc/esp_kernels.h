@@ -15,9 +15,9 @@ struct Staged {
     float *xh, *yh, *zh, *xl, *yl, *zl;
 };
 
-// FP32C tile groups: point charges, then one group per L (long- and
-// short-range tiles of that L together).
-constexpr int kMaxTileGroups = 6;
+// FP32C tile groups: FP64 point charges, FP32 point charges, then one group
+// per L (long- and short-range tiles of that L together).
+constexpr int kMaxTileGroups = 7;
 
 struct EvalArgs {
     int n_pos;
@@ -104,9 +104,15 @@ size_t potential_smem_bytes(int precision, int tile_size);
 // FP32C (64,{2,4}), (128,{1,2,4}), (256,{1,2}).
 bool potential_shape_supported(int precision, int threads, int ppt);
 // Few positions per call (n <= kSmallN): environment entries spread over the
-// threads of n_splits CTAs, FP64 throughout, partial[split][n], then one CTA
-// per position sums the partials into V in a fixed order.
-constexpr int kSmallN = 16;
+// threads of n_splits CTAs, partial[split][n], then one CTA per position
+// sums the partials into V in a fixed order.  Entries are evaluated in FP64,
+// except the FP32 point charges (class kClassPoint32) when fp32 is set: those
+// take the compensated FP32 form of the main kernel (hi/lo offsets, symmetric
+// rsqrt, low word of the charge) and add into the thread's FP64 sums.
+constexpr int kSmallN = 128;
+constexpr int kSmallChunk = 16;      // positions held in registers per pass
+constexpr int kSmallNDistributions = 16; // calls above this many positions take the
+                                         // few-position path only for environments of point charges
 struct SmallArgs {
     int n_pos;
     int n_tiles;
@@ -114,7 +120,10 @@ struct SmallArgs {
     double cx, cy, cz;     // QM centre
     const TileMeta *tiles;
     const double *rec64;
+    const float *rec32;
     const double *boys64;
+    double quantum;        // coordinate grid of the FP32 hi words
+    int fp32;              // FP32 point charges in compensated FP32
     double *partial;
 };
 int small_n_splits(int n_tiles, int num_sms);

@@ -87,9 +87,24 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         const bool pts = m.cls == kClassPoint;
         const float4 *src = pts ? reinterpret_cast<const float4 *>(a.rec64 + m.off64)
                                 : reinterpret_cast<const float4 *>(a.rec32 + m.off32);
-        const int nvec = pts ? m.n * 2 : (m.n * rec32_stride(m.cls & 7)) / 4;
+        const int nvec = pts ? m.n * 2 : (m.n * rec32_stride_cls(m.cls)) / 4;
         copy_tile(s_tile4, src, nvec);
         __syncthreads();
+        if (m.cls == kClassPoint32) {
+            // small point charges: the far form of an L = 0 record, no near path
+            const float *s_rec = reinterpret_cast<const float *>(s_tile4);
+            if constexpr (PPT % 2 == 0) {
+                f2 wq[NP];
+                tile_f32c2<0, NP, true, false, false>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);
+            } else {
+                bool none[PPT];
+#pragma unroll
+                for (int q = 0; q < PPT; ++q)
+                    none[q] = false;
+                tile_f32c<0, PPT, true, false, false>(s_rec, m.n, ch, cl, none, S, Cc, s_boys);
+            }
+            continue;
+        }
         if (pts) {
             double c64[PPT][3];
 #pragma unroll
@@ -242,7 +257,7 @@ __device__ __forceinline__ void cta_f64(const EvalArgs &a, int bx, int split, fl
     for (int t = split; t < a.n_tiles; t += a.n_splits) {
         const TileMeta m = a.tiles[t];
         __syncthreads();
-        const bool pts = m.cls == kClassPoint;
+        const bool pts = is_point_class(m.cls);
         const int nvec = pts ? m.n * 2 : (m.n * rec64_stride(m.cls & 7)) / 2;
         copy_tile(smem4, reinterpret_cast<const float4 *>(a.rec64 + m.off64), nvec);
         __syncthreads();

@@ -533,33 +533,54 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         kept_charges += pts[size_t(i)].Z != 0.0;
     out.n_point_charges = kept_charges;
 
+    // FP64 point tiles (|Z| above the FP32 threshold: nuclei, merged
+    // monopoles), then FP32 point tiles (small charges such as the paper's
+    // density cells), each in Morton order
+    const double q32 = opt.point32_max_charge < 0.0 ? kDefaultPoint32Max : opt.point32_max_charge;
     size_t off64 = 0, off32 = 0;
     std::vector<double> pbuf;
-    for (int64_t s = 0; s < n_pts;) {
-        TileMeta m;
-        std::memset(&m, 0, sizeof(m));
-        m.cls = kClassPoint;
-        m.off64 = int32_t(off64);
-        pbuf.clear();
-        double qsum = 0.0;
-        while (s < n_pts && m.n < tile) {
-            const PointQ &c = pts[size_t(pidx[size_t(s)])];
-            ++s;
-            if (c.Z == 0.0)
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool small = pass == 1;
+        for (int64_t s = 0; s < n_pts;) {
+            TileMeta m;
+            std::memset(&m, 0, sizeof(m));
+            m.cls = small ? kClassPoint32 : kClassPoint;
+            m.off64 = int32_t(off64);
+            m.off32 = int32_t(off32);
+            pbuf.clear();
+            double qsum = 0.0;
+            while (s < n_pts && m.n < tile) {
+                const PointQ &c = pts[size_t(pidx[size_t(s)])];
+                ++s;
+                if (c.Z == 0.0 || (std::fabs(c.Z) <= q32) != small)
+                    continue;
+                for (int d = 0; d < 3; ++d)
+                    pbuf.push_back(c.x[d]);
+                pbuf.push_back(c.Z);
+                qsum += std::fabs(c.Z);
+                ++m.n;
+                if (small) {
+                    // FP32 record in the L = 0 layout: centre hi / lo, M_000 = Z + lo word
+                    const size_t b32 = out.rec32.size();
+                    out.rec32.resize(b32 + rec32_stride(0), 0.0f);
+                    for (int d = 0; d < 3; ++d) {
+                        const double h = quantize_hi(c.x[d], out.coord_quantum);
+                        out.rec32[b32 + d] = float(h);
+                        out.rec32[b32 + rec32_lo(0) + d] = float(c.x[d] - h);
+                    }
+                    out.rec32[b32 + rec32_m(0)] = float(c.Z);
+                    out.rec32[b32 + rec32_lo(0) + 3] = float(c.Z - double(float(c.Z)));
+                }
+            }
+            if (m.n == 0)
                 continue;
-            for (int d = 0; d < 3; ++d)
-                pbuf.push_back(c.x[d]);
-            pbuf.push_back(c.Z);
-            qsum += std::fabs(c.Z);
-            ++m.n;
+            bounding_sphere(pbuf.data(), kPointStride64, m.n, m);
+            m.qabs = float(qsum);
+            out.rec64.insert(out.rec64.end(), pbuf.begin(), pbuf.end());
+            off64 += pbuf.size();
+            off32 = out.rec32.size();
+            out.tiles.push_back(m);
         }
-        if (m.n == 0)
-            continue;
-        bounding_sphere(pbuf.data(), kPointStride64, m.n, m);
-        m.qabs = float(qsum);
-        out.rec64.insert(out.rec64.end(), pbuf.begin(), pbuf.end());
-        off64 += pbuf.size();
-        out.tiles.push_back(m);
     }
 
     // distribution tiles: never span a class or an exponent band

@@ -307,7 +307,7 @@ void split_tiles(esp_surrogate *s)
     for (const TileMeta &m : s->ctx->env.tiles) {
         const double d = std::sqrt(double(m.cx) * m.cx + double(m.cy) * m.cy + double(m.cz) * m.cz) - double(m.rad);
         bool far = d >= Rs;
-        if (far && m.cls != kClassPoint)
+        if (far && !is_point_class(m.cls))
             far = double(m.pmin) * (d - R) * (d - R) >= 30.0;
         (far ? s->far_tiles : s->near_tiles).push_back(m);
         (far ? s->n_far_entries : s->n_near_entries) += m.n;
@@ -546,7 +546,7 @@ esp_status nearby_point_charges(esp_surrogate *s, double reach, std::vector<doub
     const esp_ctx *c = s->ctx;
     pts.clear();
     for (const TileMeta &m : c->env.tiles) {
-        if (m.cls != kClassPoint)
+        if (!is_point_class(m.cls))
             continue;
         const double d = std::sqrt(double(m.cx) * m.cx + double(m.cy) * m.cy + double(m.cz) * m.cz) - double(m.rad);
         if (d > reach)

@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("qm_center", ctypes.c_double * 3), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("tile_size", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("positions_per_thread", ctypes.c_int32),
-                ("pair_splits", ctypes.c_int32), ("flags", ctypes.c_int32), ("near_radius", ctypes.c_double)]
+                ("pair_splits", ctypes.c_int32), ("flags", ctypes.c_int32), ("near_radius", ctypes.c_double),
+                ("point32_max_charge", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -197,6 +198,12 @@ def load(build_if_missing: bool = False):
     lib.esp_surrogate_debug_net.restype = ctypes.c_int
     lib.esp_surrogate_destroy.argtypes = [P]
     lib.esp_surrogate_destroy.restype = None
+    lib.esp_graph_create.argtypes = [P, P, i64, P, ctypes.POINTER(P)]
+    lib.esp_graph_create.restype = ctypes.c_int
+    lib.esp_graph_launch.argtypes = [P]
+    lib.esp_graph_launch.restype = ctypes.c_int
+    lib.esp_graph_destroy.argtypes = [P]
+    lib.esp_graph_destroy.restype = None
     lib.esp_work_census.argtypes = [P, P, i64, P]
     lib.esp_work_census.restype = ctypes.c_int
     lib.esp_measure_peaks.argtypes = [i32, ctypes.POINTER(Peaks)]
@@ -258,7 +265,7 @@ class Environment:
 
     def __init__(self, nuclei_xyz, nuclei_Z, pairs, precision="fp32c", screen_tol=1e-12,
                  qm_center=(0.0, 0.0, 0.0), stream=None, device=-1, tile_size=0, threads_per_block=0,
-                 positions_per_thread=0, pair_splits=0, near_radius=-1.0, flags=0):
+                 positions_per_thread=0, pair_splits=0, near_radius=-1.0, flags=0, point32_max_charge=-1.0):
         lib = load()
         opt = default_options()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -272,6 +279,7 @@ class Environment:
         opt.pair_splits = int(pair_splits)
         opt.near_radius = float(near_radius)
         opt.flags = int(flags)
+        opt.point32_max_charge = float(point32_max_charge)
         ch = pack_charges(nuclei_xyz, nuclei_Z)
         pr = pack_pairs(pairs)
         w = np.ascontiguousarray(pairs.w, np.float64)
@@ -369,11 +377,11 @@ class Environment:
         """Terms per (L, short-range, Boys band) at host positions (esp_work_census):
         {"far30": [5], "mid": [5], "far45": [5] ... } keyed as below, counts over all positions."""
         pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
-        c = np.zeros(31, np.int64)
+        c = np.zeros(32, np.int64)
         _check(load().esp_work_census(self._ctx, pos.ctypes.data, pos.shape[0], c.ctypes.data))
         t = c[:30].reshape(2, 5, 3)  # [short][L][band]
         return {"positions": int(pos.shape[0]), "T_lt_30": t[:, :, 0].tolist(), "T_30_45": t[:, :, 1].tolist(),
-                "T_ge_45": t[:, :, 2].tolist(), "point_terms": int(c[30])}
+                "T_ge_45": t[:, :, 2].tolist(), "point_terms": int(c[30]), "point32_terms": int(c[31])}
 
     def debug_host_eval(self, positions: np.ndarray) -> np.ndarray:
         """Test hook: evaluate the built tiles on the host in FP64 (never used by eval)."""
@@ -409,6 +417,42 @@ def debug_boys(precision, nmax: int, T: float) -> np.ndarray:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _check(load().esp_debug_boys(p, int(nmax), float(T), F.ctypes.data))
     return F
+
+
+class Graph:
+    """The few-position evaluation of a fixed device buffer, captured once and
+    replayed per call (esp_graph_*).  positions [n, 3] and out [n] are CUDA
+    float64 tensors that stay in place; write new positions into `positions`
+    between launches."""
+
+    def __init__(self, env, positions, out):
+        self.env, self.positions, self.out = env, positions, out
+        g = ctypes.c_void_p()
+        _check(load().esp_graph_create(env.handle, ctypes.c_void_p(positions.data_ptr()), int(positions.shape[0]),
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.byref(g)))
+        self._g = g
+        env._dependents.add(self)
+
+    def launch(self):
+        _check(load().esp_graph_launch(self._g))
+        return self.out
+
+    def close(self):
+        if getattr(self, "_g", None) and self._g.value:
+            load().esp_graph_destroy(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Batch:

@@ -186,13 +186,47 @@ def test_realistic_full_size_sampled():
 # ---------------------------------------------------------------------------
 # the paper's literal workload: point cells + nuclei, a few positions per call
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("n_pos", [1, 7, 128])
+@pytest.mark.parametrize("n_pos", [1, 7, 16, 17, 64, 128, 129])
 def test_point_cells(n_pos):
+    """The paper's cells (small charges, summed in compensated FP32 under
+    FP32C) and nuclei (FP64): FP64 at 1e-10 relative, FP32C at 2e-6 Ha per
+    point, through the few-position path (n <= 128) and the main path."""
     wl = point_cells_environment(1234 + n_pos, n_cells=20000, n_nuclei=36, n_positions=n_pos)
     ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
     for prec in ("fp64", "fp32c"):
         with env_of(wl, prec) as env:
-            check_fp64(env.eval(wl.positions), ref, "cells " + prec)
+            V = env.eval(wl.positions)
+            if prec == "fp64":
+                check_fp64(V, ref, "cells fp64")
+            else:
+                check_fp32(V, ref, "cells fp32c")
+    # every point charge in FP64 (threshold 0): the FP64 accuracy again
+    with env_of(wl, "fp32c", point32_max_charge=0.0) as env:
+        check_fp64(env.eval(wl.positions), ref, "cells, all FP64 points")
+
+
+def test_point_cells_graph_replay():
+    """The captured few-position call: replays equal direct calls, and new
+    positions written into the buffer between replays are picked up."""
+    torch = pytest.importorskip("torch")
+    wl = point_cells_environment(4321, n_cells=50000, n_nuclei=36, n_positions=256)
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    stream = torch.cuda.current_stream()
+    with env_of(wl, "fp32c", stream=stream.cuda_stream) as env:
+        for n in (1, 16, 128):
+            buf = torch.from_numpy(wl.positions[:n].copy()).cuda()
+            out = torch.empty(n, dtype=torch.float64, device="cuda")
+            with esp.Graph(env, buf, out) as g:
+                g.launch()
+                stream.synchronize()
+                direct = env.eval(buf)
+                stream.synchronize()
+                assert torch.equal(out, direct)
+                check_fp32(out.cpu().numpy(), ref[:n], "graph n=%d" % n)
+                buf.copy_(torch.from_numpy(wl.positions[128:128 + n].copy()))
+                g.launch()
+                stream.synchronize()
+                check_fp32(out.cpu().numpy(), ref[128:128 + n], "graph n=%d, second buffer" % n)
 
 
 # ---------------------------------------------------------------------------

@@ -256,3 +256,21 @@ def test_batch_refuses_host_only_contexts(lib):
     assert lib.esp_batch_create(arr, 1, None, ctypes.byref(b)) == esp.ESP_ERR_STATE
     assert lib.esp_batch_create(arr, 0, None, ctypes.byref(b)) == esp.ESP_ERR_INVALID
     lib.esp_batch_destroy(None)
+
+
+def test_small_point_charges_fp32_class_on_host():
+    """Small point charges (the paper's cells) go to the FP32 point class; the
+    kernels' own per-tile code run on the host meets the FP32C bound against
+    the oracle, and with the threshold at 0 every charge stays FP64."""
+    from workloads import point_cells_environment
+    wl = point_cells_environment(77, n_cells=3000, n_nuclei=12, n_positions=20)
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    with esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c",
+                         flags=esp.FLAG_HOST_ONLY) as env:
+        assert env.info()["n_point_charges"] == 3012
+        V = env.debug_host_eval(wl.positions)
+    assert np.abs(V - ref).max() <= 2e-6
+    with esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp64",
+                         flags=esp.FLAG_HOST_ONLY, point32_max_charge=0.0) as env:
+        V = env.debug_host_eval(wl.positions)
+    assert np.allclose(V, ref, rtol=1e-12, atol=1e-12)
