@@ -520,6 +520,58 @@ def latency_leg(args, esp, torch, stream, oracle_mod=None):
     return out
 
 
+def clients_leg(args, esp, torch, wl):
+    """Several host threads sharing one GPU context through the library's
+    server (the paper's proposal of several processes sharing one GPU): each
+    client submits 64 walkers x 32 electrons per step; throughput for 1, 2 and
+    4 clients against one, and one client overlapping host work (a fixed
+    matrix product) with its request."""
+    import threading
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c")
+    per = 64 * 32
+    steps = 6
+    rng = np.random.default_rng(11)
+    pos = wl.positions[rng.choice(wl.n_positions, size=(4, steps, per))]
+    res = {"workload": "realistic environment, %d positions (64 walkers x 32 electrons) per client per step" % per}
+    base = None
+    with esp.Server(env, 4 * per) as srv:
+        outs = np.zeros((4, steps, per))
+        srv.wait(srv.submit(pos[0, 0], outs[0, 0]))  # warm-up
+        for nc in (1, 2, 4):
+            def client(c):
+                for k in range(steps):
+                    srv.wait(srv.submit(pos[c, k], outs[c, k]))
+            th = [threading.Thread(target=client, args=(c,)) for c in range(nc)]
+            b0 = srv.stats()["batches"]
+            t0 = time.perf_counter()
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            dt = time.perf_counter() - t0
+            rate = nc * steps * per / dt
+            base = base or rate
+            res["clients_%d" % nc] = {"positions_per_s": rate, "vs_one_client": rate / base,
+                                      "batches": srv.stats()["batches"] - b0}
+        # overlap: host work between submit and wait, against the two in sequence
+        A = np.random.default_rng(12).normal(size=(600, 600))
+        t0 = time.perf_counter()
+        for k in range(steps):
+            srv.wait(srv.submit(pos[0, k], outs[0, k]))
+            A @ A
+        seq = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for k in range(steps):
+            t = srv.submit(pos[0, k], outs[0, k])
+            A @ A
+            srv.wait(t)
+        ovl = time.perf_counter() - t0
+        res["overlap"] = {"sequential_ms_per_step": seq * 1e3 / steps, "overlapped_ms_per_step": ovl * 1e3 / steps,
+                          "host_work": "600 x 600 matrix product per step"}
+    env.close()
+    return res
+
+
 def host_units(wl):
     """The library's unit count of the environment (distributions after its
     screening and merges + point charges), from a host-only build that touches
@@ -829,6 +881,7 @@ def main(argv=None):
         if oracle_mod is not None:
             leg["accuracy"], _, _ = accuracy_leg(wl2, "realistic", env2, V2, E2, torch, oracle_mod)
         out["realistic"] = leg
+        out["clients"] = clients_leg(args, esp, torch, wl2)
         if not args.no_surrogate:
             sur_legs["realistic"] = surrogate_leg(args, env2, wl2, workload_label(wl2, "realistic"), torch, stream,
                                                   flush, h2["ms_per_step"], V2, ref_fn=fp64_ref(env2))

@@ -234,6 +234,40 @@ esp_status esp_graph_launch(esp_graph *g);
 void esp_graph_destroy(esp_graph *g);
 
 /* ------------------------------------------------------------------------
+ * Several clients sharing one GPU context.  The paper runs one process per
+ * core with a GPU each and proposes sharing one GPU among several processes
+ * with OpenMP threads on the host (Introduction, Discussions).  A server owns
+ * a context and one worker thread; any number of host threads submit their
+ * positions and get a ticket; the worker takes every request queued when it
+ * wakes, evaluates them together in one esp_eval (so small requests fill the
+ * GPU together) and scatters the potentials back.  A client that does host
+ * work between submit and wait overlaps it with the evaluation.
+ * ------------------------------------------------------------------------ */
+typedef struct esp_server esp_server;
+
+/* Start a server on ctx with pinned staging for max_positions positions per
+ * batch.  While the server exists its worker thread uses ctx: other calls on
+ * ctx return ESP_ERR_STATE when they meet it busy.  Errors: ESP_ERR_INVALID,
+ * ESP_ERR_STATE (host-only or invalid context), ESP_ERR_OOM, ESP_ERR_CUDA. */
+esp_status esp_server_create(esp_ctx *ctx, int64_t max_positions, esp_server **out);
+
+/* Queue positions [n][3] (host memory, 1 <= n <= max_positions) whose
+ * potentials go to V_out [n] (host); both must stay valid until the wait for
+ * the returned ticket returns.  Thread-safe, does not block on the GPU. */
+esp_status esp_server_submit(esp_server *s, const double *positions, int64_t n, double *V_out, int64_t *ticket);
+
+/* Block until the ticket's potentials are in its V_out.  Thread-safe.
+ * Returns the batch's error if its evaluation failed. */
+esp_status esp_server_wait(esp_server *s, int64_t ticket);
+
+/* Batches evaluated and positions served so far (either pointer may be NULL). */
+esp_status esp_server_stats(esp_server *s, int64_t *batches, int64_t *positions);
+
+/* Finish the queued requests, stop the worker and free the server (not its
+ * context).  NULL is a no-op. */
+void esp_server_destroy(esp_server *s);
+
+/* ------------------------------------------------------------------------
  * Batched evaluation of many independent systems (environment, positions).
  * An FMO calculation has many fragments and fragment pairs (Eq. FMO), each
  * with its own environment field, and QMC runs many walkers: the batch
@@ -476,6 +510,25 @@ esp_status esp_debug_host_eval(const esp_ctx *ctx, const double *positions, int6
  * Synchronous; allocates and frees a small device buffer.  Errors:
  * ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_CUDA, ESP_ERR_OOM. */
 esp_status esp_work_census(esp_ctx *ctx, const double *positions, int64_t n, int64_t *counts);
+
+/* ------------------------------------------------------------------------
+ * The paper's coalescing study (Results: Eq. coalease vs Eq. incoalease,
+ * Table Single Core performances; 6.0x kernel-only gain on its GPU), re-run
+ * on this GPU as a measurement, not an evaluation path: the potential of the
+ * context's point charges (cells and nuclei) at one position, by the paper's
+ * kernel structure (blocks of 256 threads, n_loop iterations per thread,
+ * shared-memory block sum) with the coalesced mapping (cell = l N_B N_th +
+ * b N_th + j) or the incoalesced one (cell = (b N_th + j) n_loop + l), in FP64
+ * or FP32 arithmetic (FP64 sums).
+ * ------------------------------------------------------------------------ */
+/*   position   host [3] (bohr);  incoalesced: 0 or 1;  fp64: 0 (FP32) or 1;
+ *   n_loop     iterations per thread (the paper used 9);  reps: timed launches;
+ *   V_out      host: the sum;  ms_out (nullable): mean time of one launch pair
+ *              (the block kernel and the final sum), CUDA events on the stream.
+ * Synchronous.  Errors: ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_UNSUPPORTED (no
+ * point charges), ESP_ERR_OOM, ESP_ERR_CUDA. */
+esp_status esp_study_cell_sum(esp_ctx *ctx, const double *position, int32_t incoalesced, int32_t fp64,
+                              int32_t n_loop, int32_t reps, double *V_out, double *ms_out);
 
 /* ------------------------------------------------------------------------
  * Measured pipe peaks of the GPU: the denominators of the potential kernels'

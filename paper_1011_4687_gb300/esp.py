@@ -204,6 +204,18 @@ def load(build_if_missing: bool = False):
     lib.esp_graph_launch.restype = ctypes.c_int
     lib.esp_graph_destroy.argtypes = [P]
     lib.esp_graph_destroy.restype = None
+    lib.esp_server_create.argtypes = [P, i64, ctypes.POINTER(P)]
+    lib.esp_server_create.restype = ctypes.c_int
+    lib.esp_server_submit.argtypes = [P, P, i64, P, ctypes.POINTER(i64)]
+    lib.esp_server_submit.restype = ctypes.c_int
+    lib.esp_server_wait.argtypes = [P, i64]
+    lib.esp_server_wait.restype = ctypes.c_int
+    lib.esp_server_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.esp_server_stats.restype = ctypes.c_int
+    lib.esp_server_destroy.argtypes = [P]
+    lib.esp_server_destroy.restype = None
+    lib.esp_study_cell_sum.argtypes = [P, P, i32, i32, i32, i32, P, P]
+    lib.esp_study_cell_sum.restype = ctypes.c_int
     lib.esp_work_census.argtypes = [P, P, i64, P]
     lib.esp_work_census.restype = ctypes.c_int
     lib.esp_measure_peaks.argtypes = [i32, ctypes.POINTER(Peaks)]
@@ -383,6 +395,15 @@ class Environment:
         return {"positions": int(pos.shape[0]), "T_lt_30": t[:, :, 0].tolist(), "T_30_45": t[:, :, 1].tolist(),
                 "T_ge_45": t[:, :, 2].tolist(), "point_terms": int(c[30]), "point32_terms": int(c[31])}
 
+    def study_cell_sum(self, position, incoalesced: bool, fp64: bool, n_loop: int = 9, reps: int = 20):
+        """The paper's coalescing study on this context's point charges at one
+        position: (V, ms per launch) of the coalesced or incoalesced mapping."""
+        p = np.ascontiguousarray(position, np.float64).reshape(3)
+        v, ms = ctypes.c_double(), ctypes.c_double()
+        _check(load().esp_study_cell_sum(self._ctx, p.ctypes.data, int(bool(incoalesced)), int(bool(fp64)),
+                                         int(n_loop), int(reps), ctypes.byref(v), ctypes.byref(ms)))
+        return v.value, ms.value
+
     def debug_host_eval(self, positions: np.ndarray) -> np.ndarray:
         """Test hook: evaluate the built tiles on the host in FP64 (never used by eval)."""
         pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
@@ -441,6 +462,57 @@ class Graph:
         if getattr(self, "_g", None) and self._g.value:
             load().esp_graph_destroy(self._g)
             self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """One context shared by several host threads (esp_server_*): submit()
+    queues host positions and returns a ticket, wait() blocks until that
+    request's potentials are in its output array."""
+
+    def __init__(self, env, max_positions):
+        self.env = env
+        h = ctypes.c_void_p()
+        _check(load().esp_server_create(env.handle, int(max_positions), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+        env._dependents.add(self)
+
+    def submit(self, positions: np.ndarray, out: np.ndarray) -> int:
+        pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != pos.shape[0]:
+            raise ValueError("out must be a contiguous float64 array of one value per position")
+        t = ctypes.c_int64()
+        _check(load().esp_server_submit(self._h, pos.ctypes.data, pos.shape[0], out.ctypes.data, ctypes.byref(t)))
+        self._keep[t.value] = (pos, out)  # keep the buffers alive until the wait
+        return t.value
+
+    def wait(self, ticket: int):
+        try:
+            _check(load().esp_server_wait(self._h, int(ticket)))
+        finally:
+            self._keep.pop(int(ticket), None)
+
+    def stats(self):
+        b, n = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().esp_server_stats(self._h, ctypes.byref(b), ctypes.byref(n)))
+        return {"batches": b.value, "positions": n.value}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().esp_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -247,7 +247,8 @@ def test_few_positions_all_classes(n_pos):
         with env_of(wl, prec) as env:
             assert min(env.info()["n_by_L"]) > 0  # every L class present
             V = env.eval(pos)
-            if prec == "fp64" or n_pos <= 16:
+            # (FP32C sums small point charges in compensated FP32 on every path)
+            if prec == "fp64":
                 check_fp64(V, ref, "few %d %s" % (n_pos, prec))
             else:
                 check_fp32(V, ref, "few %d %s" % (n_pos, prec))
@@ -355,3 +356,18 @@ def test_fp64_near_path_when_enabled():
         V, E = env.eval_walkers(wl.positions, wl.n_walkers, wl.n_elec)
     check_fp32(V, ref, "near 2.0")
     assert np.abs(E - oracle.walker_energies(ref, wl.n_walkers, wl.n_elec)).max() <= FP32_WALKER
+
+
+# ---------------------------------------------------------------------------
+# the paper's coalescing study: both thread mappings compute the same sum
+# ---------------------------------------------------------------------------
+def test_coalescing_study_mappings_agree_with_oracle():
+    wl = point_cells_environment(999, n_cells=30000, n_nuclei=36, n_positions=2)
+    ref = oracle.potential(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, wl.positions)
+    with env_of(wl, "fp32c") as env:
+        for k in range(2):
+            for inco in (False, True):
+                v64, ms = env.study_cell_sum(wl.positions[k], inco, True, n_loop=9, reps=2)
+                assert abs(v64 - ref[k]) <= FP64_REL * max(abs(ref[k]), 1.0) and ms > 0
+                v32, _ = env.study_cell_sum(wl.positions[k], inco, False, n_loop=9, reps=2)
+                assert abs(v32 - ref[k]) <= 1e-5  # plain FP32 terms, FP64 sums
