@@ -572,6 +572,28 @@ def clients_leg(args, esp, torch, wl):
     return res
 
 
+def coalescing_leg(esp, reps=50):
+    """The paper's coalescing study on its own workload shape (268,782 cells +
+    36 nuclei, one position): its kernel structure (blocks of 256 threads, 9
+    iterations each, shared-memory block sum) with the coalesced and the
+    incoalesced thread-to-cell mapping, FP64 and FP32 arithmetic; kernel time
+    per launch (CUDA events) and the incoalesced/coalesced ratio, next to the
+    paper's 6.0x (kernel only, GTX 275)."""
+    from workloads import point_cells_environment
+    wl = point_cells_environment(seed=1011 * 100 + 6, n_cells=268782, n_nuclei=36, n_positions=1)
+    env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs, precision="fp32c")
+    out = {"workload": "268,782 cells + 36 nuclei, one position; 256 threads x 9 iterations per block (the "
+                       "paper's N_th and N_loop), %d blocks" % ((268818 + 256 * 9 - 1) // (256 * 9)),
+           "paper_kernel_ratio": 6.0}
+    for prec, fp64 in (("fp64", True), ("fp32", False)):
+        vc, tc = env.study_cell_sum(wl.positions[0], False, fp64, n_loop=9, reps=reps)
+        vi, ti = env.study_cell_sum(wl.positions[0], True, fp64, n_loop=9, reps=reps)
+        out[prec] = {"coalesced_us": tc * 1e3, "incoalesced_us": ti * 1e3, "incoalesced_over_coalesced": ti / tc,
+                     "abs_diff_ha": abs(vc - vi)}
+    env.close()
+    return out
+
+
 def host_units(wl):
     """The library's unit count of the environment (distributions after its
     screening and merges + point charges), from a host-only build that touches
@@ -783,6 +805,8 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-systems leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--no-latency", action="store_true", help="skip the one-position-per-call leg")
+    ap.add_argument("--coalescing-study", action="store_true",
+                    help="run only the paper's coalesced vs incoalesced study and print its JSON")
     ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched leg")
     ap.add_argument("--walkers", type=int, default=0,
                     help="walkers per GPU of the headline workload (0: the configuration's own; fewer only for "
@@ -791,6 +815,11 @@ def main(argv=None):
     keep_heap()
     if args.impl == "reference":
         return run_reference(args)
+    if args.coalescing_study:
+        from paper_1011_4687_gb300 import build_lib, esp
+        build_lib.build()
+        print(json.dumps({"coalescing_study": coalescing_leg(esp)}), flush=True)
+        return 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -892,6 +921,7 @@ def main(argv=None):
         del batch_wls
     if not args.no_latency:
         out["few_positions_per_call"] = latency_leg(args, esp, torch, stream, oracle_mod)
+        out["coalescing_study"] = coalescing_leg(esp)
     if not args.no_surrogate:
         sur_legs["small"] = small_surrogate_leg(args, torch, stream, flush, oracle_mod)
         out["surrogate"] = sur_legs
