@@ -807,6 +807,7 @@ def main(argv=None):
     ap.add_argument("--no-latency", action="store_true", help="skip the one-position-per-call leg")
     ap.add_argument("--coalescing-study", action="store_true",
                     help="run only the paper's coalesced vs incoalesced study and print its JSON")
+    ap.add_argument("--study-reps", type=int, default=50, help="timed launches per variant of the study")
     ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched leg")
     ap.add_argument("--walkers", type=int, default=0,
                     help="walkers per GPU of the headline workload (0: the configuration's own; fewer only for "
@@ -818,7 +819,7 @@ def main(argv=None):
     if args.coalescing_study:
         from paper_1011_4687_gb300 import build_lib, esp
         build_lib.build()
-        print(json.dumps({"coalescing_study": coalescing_leg(esp)}), flush=True)
+        print(json.dumps({"coalescing_study": coalescing_leg(esp, args.study_reps)}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

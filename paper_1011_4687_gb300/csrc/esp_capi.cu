@@ -94,11 +94,21 @@ void esp::set_tile_groups(const std::vector<TileMeta> &T, TileView &v)
     const double kPointCost = 12.0, kPoint32Cost = 10.0;
     v.n_tiles = int(T.size());
     int64_t n_small = 0, n_all = 0;
+    v.n_p32 = 0;
+    v.p32_off = 0;
+    bool contiguous = true;
     for (const TileMeta &m : T) {
         n_all += m.n;
-        n_small += m.cls == kClassPoint32 ? m.n : 0;
+        if (m.cls != kClassPoint32)
+            continue;
+        if (n_small == 0)
+            v.p32_off = m.off32;
+        else if (int64_t(m.off32) != v.p32_off + n_small * rec32_stride(0))
+            contiguous = false;
+        n_small += m.n;
     }
     v.point_heavy = n_all > 0 && n_small * 10 >= n_all * 9;
+    v.n_p32 = contiguous ? int(n_small) : 0;
     v.n_groups = 1;
     v.grp_tile[0] = 0;
     v.grp_tile[1] = int(T.size());
@@ -222,7 +232,9 @@ esp_status pipeline(esp_ctx *c, const TileView &v, int prec, const double *d_pos
         sa.rec32 = a.rec32;
         sa.boys64 = a.boys64;
         sa.quantum = c->env.coord_quantum;
-        sa.fp32 = prec == 1;
+        sa.fp32 = prec == 1 && v.n_p32 > 0;
+        sa.p32_off = v.p32_off;
+        sa.n_p32 = v.n_p32;
         sa.partial = a.partial;
         if ((e = launch_small_n(sa, splits, dV, s)) != cudaSuccess)
             return cuda_fail(e, "launching the few-position kernels");

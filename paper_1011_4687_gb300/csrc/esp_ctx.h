@@ -147,6 +147,10 @@ struct TileView {
     int grp_tile[kMaxTileGroups + 1] = {0, 0};
     double grp_work[kMaxTileGroups] = {0.0};
     bool point_heavy = false; // >= 90 % of the entries are FP32 point charges
+    // FP32 point charges of the view: their records are contiguous in rec32
+    // (the builder emits those tiles one after the other)
+    int64_t p32_off = 0;
+    int n_p32 = 0;
 };
 
 // Tile groups of a host tile list (in device order); with fewer than one

@@ -78,7 +78,9 @@ esp_status esp_graph_create(esp_ctx *ctx, const double *positions, int64_t n, do
     sa.rec32 = static_cast<const float *>(ctx->rec32.p);
     sa.boys64 = static_cast<const double *>(ctx->boys64.p);
     sa.quantum = ctx->env.coord_quantum;
-    sa.fp32 = ctx->opt.precision == ESP_FP32C;
+    sa.fp32 = ctx->opt.precision == ESP_FP32C && ctx->full.n_p32 > 0;
+    sa.p32_off = ctx->full.p32_off;
+    sa.n_p32 = ctx->full.n_p32;
     cudaError_t e = g->partial.ensure(size_t(splits) * size_t(n) * sizeof(double));
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kBatchSortThreads) batch_sort_kernel(const Bat
 // Tiles are dealt round-robin to the CTAs; entries are read straight from the
 // FP64 records (each once per call).
 // ---------------------------------------------------------------------------
-constexpr int kSmallThreads = 64; // one thread per entry of a full tile
+constexpr int kSmallThreads = 128;
 
 __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
 {
@@ -269,34 +269,48 @@ __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gtid = blockIdx.x * kSmallThreads + threadIdx.x, gthreads = gridDim.x * kSmallThreads;
     for (int q0 = 0; q0 < n; q0 += kSmallChunk) {
         const int nq = min(kSmallChunk, n - q0);
         double acc[kSmallChunk];
 #pragma unroll
         for (int q = 0; q < kSmallChunk; ++q)
             acc[q] = 0.0;
+        // FP32 point charges: one flat, coalesced pass over their contiguous
+        // records (thread g takes entries g, g + G, ...: the paper's coalesced
+        // mapping); the few terms of a thread sum in FP32, then once into FP64
+        if (a.fp32 && a.n_p32 > 0) {
+            float acc32[kSmallChunk];
+#pragma unroll
+            for (int q = 0; q < kSmallChunk; ++q)
+                acc32[q] = 0.0f;
+            for (int e = gtid; e < a.n_p32; e += gthreads) {
+                const float *r = a.rec32 + a.p32_off + (size_t)e * rec32_stride(0);
+                const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
+                const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
+                const float qh = r[rec32_m(0)], ql = r1.w;
+#pragma unroll
+                for (int q = 0; q < kSmallChunk; ++q) {
+                    if (q >= nq)
+                        break;
+                    const int k = q0 + q;
+                    const float dx = (r0.x - s_ph[k][0]) + (r1.x - s_pl[k][0]);
+                    const float dy = (r0.y - s_ph[k][1]) + (r1.y - s_pl[k][1]);
+                    const float dz = (r0.z - s_ph[k][2]) + (r1.z - s_pl[k][2]);
+                    const float rs = esp_rsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    acc32[q] += fmaf(qh, rs, ql * rs);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kSmallChunk; ++q)
+                acc[q] = double(acc32[q]);
+        }
+        // every other tile (FP64 points, distributions; FP32 points under FP64),
+        // dealt round-robin to the CTAs, one entry per thread
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
             const TileMeta m = a.tiles[t];
-            if (m.cls == kClassPoint32 && a.fp32) {
-                for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
-                    const float *r = a.rec32 + m.off32 + (size_t)j * rec32_stride(0);
-                    const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
-                    const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
-                    const float qh = r[rec32_m(0)], ql = r1.w;
-#pragma unroll
-                    for (int q = 0; q < kSmallChunk; ++q) {
-                        if (q >= nq)
-                            break;
-                        const int k = q0 + q;
-                        const float dx = (r0.x - s_ph[k][0]) + (r1.x - s_pl[k][0]);
-                        const float dy = (r0.y - s_ph[k][1]) + (r1.y - s_pl[k][1]);
-                        const float dz = (r0.z - s_ph[k][2]) + (r1.z - s_pl[k][2]);
-                        const float rs = esp_rsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                        acc[q] += double(fmaf(qh, rs, ql * rs));
-                    }
-                }
+            if (m.cls == kClassPoint32 && a.fp32)
                 continue;
-            }
             const bool pts = is_point_class(m.cls);
             const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
             for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {

@@ -124,6 +124,8 @@ struct SmallArgs {
     const double *boys64;
     double quantum;        // coordinate grid of the FP32 hi words
     int fp32;              // FP32 point charges in compensated FP32
+    int64_t p32_off;       // float offset of the FP32 point records (contiguous, n_p32 of them)
+    int n_p32;
     double *partial;
 };
 int small_n_splits(int n_tiles, int num_sms);
