@@ -264,7 +264,13 @@ ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP
             const f2 dz = (pz - ch[q][2]) + (plz - cl[q][2]);
             f2 v;
             f2 F[L + 1];
-            if constexpr (FAR) {
+            if constexpr (FAR && !SEL) {
+                // the common case: the terms go straight into the block sum
+                const f2 r2 = esp_fma(dx, dx, esp_fma(dy, dy, dz * dz));
+                boys_far<L, f2>(r2, F);
+                blk[q] = hermite_contract<L, f2, float, true>(F, dx, dy, dz, K, k0lo, blk[q]);
+                continue;
+            } else if constexpr (FAR) {
                 const f2 r2 = esp_fma(dx, dx, esp_fma(dy, dy, dz * dz));
                 boys_far<L, f2>(r2, F);
                 v = hermite_contract<L, f2, float>(F, dx, dy, dz, K, k0lo);

@@ -350,11 +350,17 @@ ESP_HD void boys_far(R r2, R (&F)[L + 1])
 // scaled offset (x, y, z) = sqrt(p) (P - C), given F_0..F_L(T).
 // ---------------------------------------------------------------------------
 // g0lo is the low word of G_0: the leading product is rounded once with it.
-template <int L, typename R, typename G_t = R>
-ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const G_t *__restrict__ G, G_t g0lo = G_t(0))
+// With ACC, the terms are added into acc0 (one fewer operation per term than
+// forming the sum and adding it); without, acc0 is ignored.
+template <int L, typename R, typename G_t = R, bool ACC = false>
+ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const G_t *__restrict__ G, G_t g0lo = G_t(0),
+                          R acc0 = R(0))
 {
     if constexpr (L == 0) {
-        return esp_fma(G[0], F[0], g0lo * F[0]);
+        if constexpr (ACC)
+            return esp_fma(G[0], F[0], esp_fma(g0lo, F[0], acc0));
+        else
+            return esp_fma(G[0], F[0], g0lo * F[0]);
     } else {
     // S[n][h] for levels n = 0..L; level n needs N <= L - n
     R S[L + 1][35];
@@ -391,7 +397,11 @@ ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const G_t *__restr
             }
         }
     }
-    R acc = esp_fma(G[0], S[0][0], g0lo * S[0][0]);
+    R acc;
+    if constexpr (ACC)
+        acc = esp_fma(G[0], S[0][0], esp_fma(g0lo, S[0][0], acc0));
+    else
+        acc = esp_fma(G[0], S[0][0], g0lo * S[0][0]);
 #pragma unroll
     for (int h = 1; h < num_hermite(L); ++h)
         acc = esp_fma(G[h], S[0][h], acc);
