@@ -585,11 +585,12 @@ def coalescing_leg(esp, reps=50):
     out = {"workload": "268,782 cells + 36 nuclei, one position; 256 threads x 9 iterations per block (the "
                        "paper's N_th and N_loop), %d blocks" % ((268818 + 256 * 9 - 1) // (256 * 9)),
            "paper_kernel_ratio": 6.0}
-    for prec, fp64 in (("fp64", True), ("fp32", False)):
-        vc, tc = env.study_cell_sum(wl.positions[0], False, fp64, n_loop=9, reps=reps)
-        vi, ti = env.study_cell_sum(wl.positions[0], True, fp64, n_loop=9, reps=reps)
-        out[prec] = {"coalesced_us": tc * 1e3, "incoalesced_us": ti * 1e3, "incoalesced_over_coalesced": ti / tc,
-                     "abs_diff_ha": abs(vc - vi)}
+    for layout, soa in (("records32B", False), ("soa", True)):
+        for prec, fp64 in (("fp64", True), ("fp32", False)):
+            vc, tc = env.study_cell_sum(wl.positions[0], False, fp64, n_loop=9, reps=reps, soa=soa)
+            vi, ti = env.study_cell_sum(wl.positions[0], True, fp64, n_loop=9, reps=reps, soa=soa)
+            out["%s_%s" % (layout, prec)] = {"coalesced_us": tc * 1e3, "incoalesced_us": ti * 1e3,
+                                             "incoalesced_over_coalesced": ti / tc, "abs_diff_ha": abs(vc - vi)}
     env.close()
     return out
 

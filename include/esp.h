@@ -358,6 +358,11 @@ typedef struct {
     uint64_t seed;             /* positions, frequencies and initial weights (1011) */
     double far_radius;         /* tiles wholly beyond this distance from the centre form the far field,
                                   bohr (12; >= qm_radius) */
+    double far_penetration;    /* ... and only if p_min (d - qm_radius)^2 >= this for every Gaussian of
+                                  the tile (d: distance of the tile's bounding sphere from the centre):
+                                  30 keeps the non-harmonic tail inside the sphere below e^-30 of the
+                                  charge; smaller values move more diffuse tiles to the far field, whose
+                                  tails the network then has to absorb (30; >= 4) */
 } esp_surrogate_cfg;
 
 typedef struct {
@@ -519,16 +524,18 @@ esp_status esp_work_census(esp_ctx *ctx, const double *positions, int64_t n, int
  * kernel structure (blocks of 256 threads, n_loop iterations per thread,
  * shared-memory block sum) with the coalesced mapping (cell = l N_B N_th +
  * b N_th + j) or the incoalesced one (cell = (b N_th + j) n_loop + l), in FP64
- * or FP32 arithmetic (FP64 sums).
+ * or FP32 arithmetic (FP64 sums), over the point records as stored (32-byte
+ * [x, y, z, Z]) or over separate x, y, z, Z arrays (soa_layout = 1).
  * ------------------------------------------------------------------------ */
 /*   position   host [3] (bohr);  incoalesced: 0 or 1;  fp64: 0 (FP32) or 1;
+ *   soa_layout 0: the 32-byte records; 1: separate arrays (FP64 or FP32 words);
  *   n_loop     iterations per thread (the paper used 9);  reps: timed launches;
  *   V_out      host: the sum;  ms_out (nullable): mean time of one launch pair
  *              (the block kernel and the final sum), CUDA events on the stream.
  * Synchronous.  Errors: ESP_ERR_INVALID, ESP_ERR_STATE, ESP_ERR_UNSUPPORTED (no
  * point charges), ESP_ERR_OOM, ESP_ERR_CUDA. */
 esp_status esp_study_cell_sum(esp_ctx *ctx, const double *position, int32_t incoalesced, int32_t fp64,
-                              int32_t n_loop, int32_t reps, double *V_out, double *ms_out);
+                              int32_t soa_layout, int32_t n_loop, int32_t reps, double *V_out, double *ms_out);
 
 /* ------------------------------------------------------------------------
  * Measured pipe peaks of the GPU: the denominators of the potential kernels'

@@ -295,9 +295,10 @@ TcLayout tc_layout()
 
 // Near / far split of the context's tiles.  A tile is far when its bounding
 // sphere lies beyond far_radius from the centre and (distributions) every
-// Gaussian of it is negligible inside the QM sphere: p_min (d - R)^2 >= 30,
-// d the distance from the centre to the sphere's nearest point, the FP32
-// kernel's own threshold for the asymptotic (multipole) form.
+// Gaussian of it is small inside the QM sphere: p_min (d - R)^2 >=
+// far_penetration (30 by default, the FP32 kernel's own threshold for the
+// asymptotic, multipole form), d the distance from the centre to the
+// bounding sphere's nearest point.
 void split_tiles(esp_surrogate *s)
 {
     const double R = 1.0 / s->inv_r, Rs = s->cfg.far_radius;
@@ -308,7 +309,7 @@ void split_tiles(esp_surrogate *s)
         const double d = std::sqrt(double(m.cx) * m.cx + double(m.cy) * m.cy + double(m.cz) * m.cz) - double(m.rad);
         bool far = d >= Rs;
         if (far && !is_point_class(m.cls))
-            far = double(m.pmin) * (d - R) * (d - R) >= 30.0;
+            far = double(m.pmin) * (d - R) * (d - R) >= s->cfg.far_penetration;
         (far ? s->far_tiles : s->near_tiles).push_back(m);
         (far ? s->n_far_entries : s->n_near_entries) += m.n;
     }
@@ -936,6 +937,7 @@ void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg)
     cfg->label_precision = ESP_FP32C;
     cfg->seed = 1011;
     cfg->far_radius = 12.0;
+    cfg->far_penetration = 30.0;
 }
 
 esp_status esp_surrogate_train(esp_ctx *ctx, const esp_surrogate_cfg *cfg_in, esp_surrogate **out)
@@ -956,7 +958,8 @@ esp_status esp_surrogate_train(esp_ctx *ctx, const esp_surrogate_cfg *cfg_in, es
         cfg.degree > kMaxExpDegree || !(cfg.qm_radius > 0.0) || !(cfg.voxel > 0.0) || !(cfg.tol > 0.0) ||
         cfg.probe_stride < 0 || cfg.n_train > (1 << 26) || cfg.n_valid > (1 << 24) ||
         (cfg.label_precision != ESP_FP64 && cfg.label_precision != ESP_FP32C) ||
-        !(cfg.far_radius >= cfg.qm_radius) || !(cfg.far_radius < 1e6))
+        !(cfg.far_radius >= cfg.qm_radius) || !(cfg.far_radius < 1e6) || !(cfg.far_penetration >= 4.0) ||
+        !(cfg.far_penetration < 1e6))
         return fail(ESP_ERR_INVALID, "bad surrogate configuration");
     BusyGuard busy(ctx->busy);
     if (!busy.acquired)

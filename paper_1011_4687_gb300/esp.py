@@ -79,7 +79,8 @@ class SurrogateCfg(ctypes.Structure):
                 ("qm_radius", ctypes.c_double), ("position_sd", ctypes.c_double), ("fourier_sigma", ctypes.c_double),
                 ("lr", ctypes.c_double), ("tol", ctypes.c_double), ("voxel", ctypes.c_double),
                 ("nucleus_exclusion", ctypes.c_double), ("probe_stride", ctypes.c_int32),
-                ("label_precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("far_radius", ctypes.c_double)]
+                ("label_precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("far_radius", ctypes.c_double),
+                ("far_penetration", ctypes.c_double)]
 
 
 class SurrogateStats(ctypes.Structure):
@@ -214,7 +215,7 @@ def load(build_if_missing: bool = False):
     lib.esp_server_stats.restype = ctypes.c_int
     lib.esp_server_destroy.argtypes = [P]
     lib.esp_server_destroy.restype = None
-    lib.esp_study_cell_sum.argtypes = [P, P, i32, i32, i32, i32, P, P]
+    lib.esp_study_cell_sum.argtypes = [P, P, i32, i32, i32, i32, i32, P, P]
     lib.esp_study_cell_sum.restype = ctypes.c_int
     lib.esp_work_census.argtypes = [P, P, i64, P]
     lib.esp_work_census.restype = ctypes.c_int
@@ -395,13 +396,15 @@ class Environment:
         return {"positions": int(pos.shape[0]), "T_lt_30": t[:, :, 0].tolist(), "T_30_45": t[:, :, 1].tolist(),
                 "T_ge_45": t[:, :, 2].tolist(), "point_terms": int(c[30]), "point32_terms": int(c[31])}
 
-    def study_cell_sum(self, position, incoalesced: bool, fp64: bool, n_loop: int = 9, reps: int = 20):
+    def study_cell_sum(self, position, incoalesced: bool, fp64: bool, n_loop: int = 9, reps: int = 20,
+                       soa: bool = False):
         """The paper's coalescing study on this context's point charges at one
-        position: (V, ms per launch) of the coalesced or incoalesced mapping."""
+        position: (V, ms per launch) of the coalesced or incoalesced mapping,
+        over the 32-byte records or separate arrays (soa)."""
         p = np.ascontiguousarray(position, np.float64).reshape(3)
         v, ms = ctypes.c_double(), ctypes.c_double()
         _check(load().esp_study_cell_sum(self._ctx, p.ctypes.data, int(bool(incoalesced)), int(bool(fp64)),
-                                         int(n_loop), int(reps), ctypes.byref(v), ctypes.byref(ms)))
+                                         int(bool(soa)), int(n_loop), int(reps), ctypes.byref(v), ctypes.byref(ms)))
         return v.value, ms.value
 
     def debug_host_eval(self, positions: np.ndarray) -> np.ndarray:

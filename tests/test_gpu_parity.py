@@ -367,7 +367,8 @@ def test_coalescing_study_mappings_agree_with_oracle():
     with env_of(wl, "fp32c") as env:
         for k in range(2):
             for inco in (False, True):
-                v64, ms = env.study_cell_sum(wl.positions[k], inco, True, n_loop=9, reps=2)
-                assert abs(v64 - ref[k]) <= FP64_REL * max(abs(ref[k]), 1.0) and ms > 0
-                v32, _ = env.study_cell_sum(wl.positions[k], inco, False, n_loop=9, reps=2)
-                assert abs(v32 - ref[k]) <= 1e-5  # plain FP32 terms, FP64 sums
+                for soa in (False, True):
+                    v64, ms = env.study_cell_sum(wl.positions[k], inco, True, n_loop=9, reps=2, soa=soa)
+                    assert abs(v64 - ref[k]) <= FP64_REL * max(abs(ref[k]), 1.0) and ms > 0
+                    v32, _ = env.study_cell_sum(wl.positions[k], inco, False, n_loop=9, reps=2, soa=soa)
+                    assert abs(v32 - ref[k]) <= 1e-5  # plain FP32 terms, FP64 sums
