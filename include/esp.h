@@ -357,7 +357,7 @@ typedef struct {
     int32_t label_precision;   /* exact kernel of the training and validation labels (ESP_FP32C; or ESP_FP64) */
     uint64_t seed;             /* positions, frequencies and initial weights (1011) */
     double far_radius;         /* tiles wholly beyond this distance from the centre form the far field,
-                                  bohr (12; >= qm_radius) */
+                                  bohr (10; >= qm_radius) */
     double far_penetration;    /* ... and only if p_min (d - qm_radius)^2 >= this for every Gaussian of
                                   the tile (d: distance of the tile's bounding sphere from the centre):
                                   30 keeps the non-harmonic tail inside the sphere below e^-30 of the

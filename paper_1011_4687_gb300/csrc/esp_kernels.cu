@@ -254,11 +254,22 @@ __global__ void __launch_bounds__(kBatchSortThreads) batch_sort_kernel(const Bat
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 128;
 
+// (s, c) += (s2, c2) with the rounding error of s + s2 kept in c (TwoSum)
+__device__ __forceinline__ void two_sum_pair(float &s, float &c, float s2, float c2)
+{
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = (c + c2) + e;
+}
+
 __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
 {
     __shared__ double s_pos[kSmallN][3];
     __shared__ float s_ph[kSmallN][3], s_pl[kSmallN][3]; // FP32 hi (on the records' grid) and lo words
-    __shared__ double s_red[kSmallThreads / 32][kSmallChunk];
+    __shared__ float s_red32[kSmallThreads / 32][kSmallChunk][2];
+    __shared__ double s_red64[kSmallThreads / 32][kSmallChunk];
     const int n = a.n_pos;
     for (int i = threadIdx.x; i < n * 3; i += kSmallThreads) {
         const double x = a.pos_in[i] - (i % 3 == 0 ? a.cx : i % 3 == 1 ? a.cy : a.cz);
@@ -267,23 +278,27 @@ __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
         s_ph[i / 3][i % 3] = float(h);
         s_pl[i / 3][i % 3] = float(x - h);
     }
+    // does this CTA evaluate any entry in FP64?  (then its FP64 sums need a
+    // FP64 reduction; FP64 instructions run at 1/64 of the FP32 rate here)
+    bool has64 = false;
+    for (int t = blockIdx.x; t < a.n_tiles && !has64; t += gridDim.x)
+        has64 = !(a.tiles[t].cls == kClassPoint32 && a.fp32);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gtid = blockIdx.x * kSmallThreads + threadIdx.x, gthreads = gridDim.x * kSmallThreads;
     for (int q0 = 0; q0 < n; q0 += kSmallChunk) {
         const int nq = min(kSmallChunk, n - q0);
+        float acc32[kSmallChunk];
         double acc[kSmallChunk];
 #pragma unroll
-        for (int q = 0; q < kSmallChunk; ++q)
+        for (int q = 0; q < kSmallChunk; ++q) {
+            acc32[q] = 0.0f;
             acc[q] = 0.0;
+        }
         // FP32 point charges: one flat, coalesced pass over their contiguous
         // records (thread g takes entries g, g + G, ...: the paper's coalesced
-        // mapping); the few terms of a thread sum in FP32, then once into FP64
+        // mapping); a thread's few terms sum in FP32
         if (a.fp32 && a.n_p32 > 0) {
-            float acc32[kSmallChunk];
-#pragma unroll
-            for (int q = 0; q < kSmallChunk; ++q)
-                acc32[q] = 0.0f;
             for (int e = gtid; e < a.n_p32; e += gthreads) {
                 const float *r = a.rec32 + a.p32_off + (size_t)e * rec32_stride(0);
                 const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
@@ -301,53 +316,67 @@ __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
                     acc32[q] += fmaf(qh, rs, ql * rs);
                 }
             }
-#pragma unroll
-            for (int q = 0; q < kSmallChunk; ++q)
-                acc[q] = double(acc32[q]);
         }
         // every other tile (FP64 points, distributions; FP32 points under FP64),
         // dealt round-robin to the CTAs, one entry per thread
-        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-            const TileMeta m = a.tiles[t];
-            if (m.cls == kClassPoint32 && a.fp32)
-                continue;
-            const bool pts = is_point_class(m.cls);
-            const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
-            for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
-                const double *r = a.rec64 + m.off64 + (size_t)j * st;
+        if (has64) {
+            for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+                const TileMeta m = a.tiles[t];
+                if (m.cls == kClassPoint32 && a.fp32)
+                    continue;
+                const bool pts = is_point_class(m.cls);
+                const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
+                for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
+                    const double *r = a.rec64 + m.off64 + (size_t)j * st;
 #pragma unroll
-                for (int q = 0; q < kSmallChunk; ++q) {
-                    if (q >= nq)
-                        break;
-                    const int k = q0 + q;
-                    if (pts) {
-                        const double dx = r[0] - s_pos[k][0], dy = r[1] - s_pos[k][1], dz = r[2] - s_pos[k][2];
-                        acc[q] += r[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
-                    } else {
-                        acc[q] += tile_f64_one_any(m.cls, r, 1, s_pos[k][0], s_pos[k][1], s_pos[k][2], a.boys64);
+                    for (int q = 0; q < kSmallChunk; ++q) {
+                        if (q >= nq)
+                            break;
+                        const int k = q0 + q;
+                        if (pts) {
+                            const double dx = r[0] - s_pos[k][0], dy = r[1] - s_pos[k][1], dz = r[2] - s_pos[k][2];
+                            acc[q] += r[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
+                        } else {
+                            acc[q] += tile_f64_one_any(m.cls, r, 1, s_pos[k][0], s_pos[k][1], s_pos[k][2],
+                                                       a.boys64);
+                        }
                     }
                 }
             }
         }
-        // fixed-order reduction per position: warp shuffles, then the warps in order
+        // fixed-order reduction per position: the FP32 sums as (sum,
+        // compensation) pairs by warp shuffles, the FP64 sums (only where this
+        // CTA has any) likewise in FP64, then the warps in order in FP64
 #pragma unroll
         for (int q = 0; q < kSmallChunk; ++q) {
             if (q >= nq)
                 break;
-            double v = acc[q];
-            for (int o = 16; o; o >>= 1)
-                v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0)
-                s_red[warp][q] = v;
+            float sv = acc32[q], cv = 0.0f;
+            for (int o = 16; o; o >>= 1) {
+                const float so = __shfl_xor_sync(0xffffffffu, sv, o), co = __shfl_xor_sync(0xffffffffu, cv, o);
+                two_sum_pair(sv, cv, so, co);
+            }
+            double v = 0.0;
+            if (has64) {
+                v = acc[q];
+                for (int o = 16; o; o >>= 1)
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+            }
+            if (lane == 0) {
+                s_red32[warp][q][0] = sv;
+                s_red32[warp][q][1] = cv;
+                s_red64[warp][q] = v;
+            }
         }
         __syncthreads();
         if (threadIdx.x < nq) {
             double v = 0.0;
             for (int w = 0; w < kSmallThreads / 32; ++w)
-                v += s_red[w][threadIdx.x];
+                v += (double(s_red32[w][threadIdx.x][0]) + double(s_red32[w][threadIdx.x][1])) +
+                     s_red64[w][threadIdx.x];
             a.partial[(size_t)blockIdx.x * n + q0 + threadIdx.x] = v;
         }
-        __syncthreads(); // s_red is reused by the next chunk
+        __syncthreads(); // the reduction buffers are reused by the next chunk
     }
 }
 

@@ -936,7 +936,7 @@ void esp_surrogate_default_cfg(esp_surrogate_cfg *cfg)
     cfg->probe_stride = 64;
     cfg->label_precision = ESP_FP32C;
     cfg->seed = 1011;
-    cfg->far_radius = 12.0;
+    cfg->far_radius = 10.0;
     cfg->far_penetration = 30.0;
 }
 
