@@ -617,7 +617,8 @@ def run_reference(args):
     units = host_units(wl)
     cfg = workload_config(wl, args.config, units, args.gpus, args.walkers not in (0, WORKLOADS[args.config]["n_walkers"]))
     per_pos = units["n_distributions"] + units["n_point_charges"]
-    sample = np.arange(args.ref_positions)
+    threads = oracle.max_threads()
+    sample = np.arange(args.ref_positions if args.ref_positions > 0 else threads)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -630,7 +631,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": val, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "evals/s", "cores": min(threads, sample.size), "kind": "oracle",
                              "sample": "%d positions of the workload per step x all %d distributions + point "
                                        "charges (the library's unit count)" % (sample.size, per_pos)},
             "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -799,7 +800,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large", choices=sorted(WORKLOADS),
                     help="headline workload (default: the largest configuration)")
-    ap.add_argument("--ref-positions", type=int, default=2, help="positions per oracle step (reference arm)")
+    ap.add_argument("--ref-positions", type=int, default=0,
+                    help="positions per oracle step (reference arm); 0 = one per host thread")
     ap.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end (host buffer) measurement")
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
     ap.add_argument("--no-secondary", action="store_true", help="skip the realistic-configuration leg")
