@@ -184,7 +184,7 @@ esp_status pipeline(esp_ctx *c, const TileView &v, int prec, const double *d_pos
     // distributions take FP64 there)
     const bool small_n = v.n_tiles > 0 && (n <= kSmallNDistributions || (n <= kSmallN && v.point_heavy));
     EvalArgs a;
-    const int splits = small_n ? small_n_splits(v.n_tiles, c->num_sms) : plan_splits(c, v, int(n), prec, 1 << 20, a);
+    const int splits = small_n ? small_n_splits(v.n_tiles, c->num_sms, int(n)) : plan_splits(c, v, int(n), prec, 1 << 20, a);
     esp_status st = ensure_scratch(c, n, splits, false, n_walkers);
     if (st != ESP_OK)
         return st;
@@ -385,18 +385,24 @@ double host_eval_f32c(const esp_ctx *c, const double *C)
         }
         if (m.cls == kClassPoint32) {
             const bool none[1] = {false};
-            tile_f32c<0, 1, true, false, false>(c->env.rec32.data() + m.off32, m.n, ch, cl, none, S, Cc, boys32);
+            const float ct0[3] = {0.0f, 0.0f, 0.0f};
+            tile_f32c<0, 1, true, false, false, false>(c->env.rec32.data() + m.off32, m.n, ch, cl, cl, ct0, none, S,
+                                                       Cc, boys32);
             continue;
         }
         bool nearq[1], farq;
         classify_tile(m, ch[0][0], ch[0][1], ch[0][2], near_r, nearq[0], farq);
         const float *r = c->env.rec32.data() + m.off32;
-#define ESP_TILE(CLS, LL, SH)                                                      \
-    case CLS:                                                                      \
-        if (farq)                                                                  \
-            tile_f32c<LL, 1, true, SH>(r, m.n, ch, cl, nearq, S, Cc, boys32);      \
-        else                                                                       \
-            tile_f32c<LL, 1, false, SH>(r, m.n, ch, cl, nearq, S, Cc, boys32);     \
+        const float ct[3] = {m.cx, m.cy, m.cz};
+        float dq[1][3];
+        for (int d = 0; d < 3; ++d)
+            dq[0][d] = (ct[d] - ch[0][d]) - cl[0][d];
+#define ESP_TILE(CLS, LL, SH)                                                          \
+    case CLS:                                                                          \
+        if (farq)                                                                      \
+            tile_f32c<LL, 1, true, SH>(r, m.n, ch, cl, dq, ct, nearq, S, Cc, boys32);  \
+        else                                                                           \
+            tile_f32c<LL, 1, false, SH>(r, m.n, ch, cl, dq, ct, nearq, S, Cc, boys32); \
         break;
         switch (m.cls) {
             ESP_TILE(0, 0, false)

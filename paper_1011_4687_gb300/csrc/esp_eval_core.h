@@ -110,7 +110,12 @@ ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double 
 //   offset = (P_hi - C_hi) + (P_lo - C_lo),
 // so that the fixed rounding of stored coordinates does not add up coherently
 // over the electrons of a walker; the leading coefficient carries a low word
-// for the same reason.  Terms are summed in FP32 over blocks of kSumBlock (4)
+// for the same reason.  REL: the records' hi words are relative to the tile's
+// grid point T (P_hi = stored + T, exact).  The far form then takes
+//   offset = (stored + P_lo) + dq,   dq = (T - C_hi) - C_lo per tile and position,
+// one addition per coordinate and term instead of three: the record's part is
+// rounded once relative to T (|P - T| is at most the tile's radius, while the
+// far form needs |P - C| of several radii), and dq once per tile.  Terms are summed in FP32 over blocks of kSumBlock (4)
 // distributions and each block sum is added into a per-position (S, C) pair by
 // TwoSum.  Positions flagged near add nothing here (the caller evaluates the
 // tile for them in FP64).
@@ -124,9 +129,10 @@ ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double 
 // ---------------------------------------------------------------------------
 // SEL: some position may be flagged near (its terms are selected away); a
 // caller that knows none is can drop the select.
-template <int L, int PPT, bool FAR, bool SHORT, bool SEL = true>
+template <int L, int PPT, bool FAR, bool SHORT, bool SEL = true, bool REL = true>
 ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[PPT][3], const float (&cl)[PPT][3],
-                      const bool (&nearq)[PPT], float (&S)[PPT], float (&Cc)[PPT], const float *__restrict__ s_boys)
+                      const float (&dq)[PPT][3], const float (&ct)[3], const bool (&nearq)[PPT], float (&S)[PPT],
+                      float (&Cc)[PPT], const float *__restrict__ s_boys)
 {
     constexpr int st = rec32_stride(L);
     constexpr int nh = num_hermite(L);
@@ -138,8 +144,19 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
         const float *r = s_rec + j * st;
         const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
         const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
-        const float px = r0.x, py = r0.y, pz = r0.z, ps = r0.w;
+        const float ps = r0.w;
         const float plx = r1.x, ply = r1.y, plz = r1.z;
+        // absolute hi words (near form), or the offset from T (far form, REL)
+        float px = r0.x, py = r0.y, pz = r0.z;
+        if constexpr (REL && FAR) {
+            px += plx;
+            py += ply;
+            pz += plz;
+        } else if constexpr (REL) {
+            px += ct[0];
+            py += ct[1];
+            pz += ct[2];
+        }
         const float k0lo = FAR ? r1.w : r[c0lo];
         float K[nh];
         if constexpr (FAR) {
@@ -162,9 +179,16 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
         }
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-            float dx = (px - ch[q][0]) + (plx - cl[q][0]);
-            float dy = (py - ch[q][1]) + (ply - cl[q][1]);
-            float dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+            float dx, dy, dz;
+            if constexpr (REL && FAR) {
+                dx = px + dq[q][0];
+                dy = py + dq[q][1];
+                dz = pz + dq[q][2];
+            } else {
+                dx = (px - ch[q][0]) + (plx - cl[q][0]);
+                dy = (py - ch[q][1]) + (ply - cl[q][1]);
+                dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+            }
             float v;
             float F[L + 1];
             if constexpr (FAR) {
@@ -223,9 +247,10 @@ ESP_HD void two_sum_acc(f2 &S, f2 &C, f2 x)
     C += e;
 }
 
-template <int L, int NP, bool FAR, bool SHORT, bool SEL>
+template <int L, int NP, bool FAR, bool SHORT, bool SEL, bool REL = true>
 ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP][3], const f2 (&cl)[NP][3],
-                       const f2 (&wq)[NP], f2 (&S)[NP], f2 (&Cc)[NP], const float *__restrict__ s_boys)
+                       const f2 (&dq)[NP][3], const float (&ct)[3], const f2 (&wq)[NP], f2 (&S)[NP], f2 (&Cc)[NP],
+                       const float *__restrict__ s_boys)
 {
     constexpr int st = rec32_stride(L);
     constexpr int nh = num_hermite(L);
@@ -235,8 +260,19 @@ ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP
         const float *r = s_rec + j * st;
         const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
         const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
-        const f2 px(r0.x), py(r0.y), pz(r0.z);
         const f2 plx(r1.x), ply(r1.y), plz(r1.z);
+        // absolute hi words (near form), or the offset from T (far form, REL)
+        float hx = r0.x, hy = r0.y, hz = r0.z;
+        if constexpr (REL && FAR) {
+            hx += r1.x;
+            hy += r1.y;
+            hz += r1.z;
+        } else if constexpr (REL) {
+            hx += ct[0];
+            hy += ct[1];
+            hz += ct[2];
+        }
+        const f2 px(hx), py(hy), pz(hz);
         const float ps = r0.w;
         const float k0lo = FAR ? r1.w : r[c0lo];
         float K[nh];
@@ -259,9 +295,16 @@ ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const f2 dx = (px - ch[q][0]) + (plx - cl[q][0]);
-            const f2 dy = (py - ch[q][1]) + (ply - cl[q][1]);
-            const f2 dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+            f2 dx, dy, dz;
+            if constexpr (REL && FAR) {
+                dx = px + dq[q][0];
+                dy = py + dq[q][1];
+                dz = pz + dq[q][2];
+            } else {
+                dx = (px - ch[q][0]) + (plx - cl[q][0]);
+                dy = (py - ch[q][1]) + (ply - cl[q][1]);
+                dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+            }
             f2 v;
             f2 F[L + 1];
             if constexpr (FAR && !SEL) {

@@ -65,7 +65,7 @@ esp_status esp_graph_create(esp_ctx *ctx, const double *positions, int64_t n, do
         return fail(ESP_ERR_OOM, "host allocation of the graph");
     g->ctx = ctx;
     g->n = int(n);
-    const int splits = small_n_splits(ctx->n_tiles, ctx->num_sms);
+    const int splits = small_n_splits(ctx->n_tiles, ctx->num_sms, int(n));
     SmallArgs sa;
     sa.n_pos = int(n);
     sa.n_tiles = ctx->n_tiles;

@@ -50,7 +50,11 @@ constexpr int kClassShortBit = 8;
 ESP_HD constexpr int num_hermite(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
 
 // FP32 record (floats), L = total angular momentum, n = num_hermite(L):
-//   [0..3]          Px_hi, Py_hi, Pz_hi, p (L = 0) or sqrt(p) (L > 0)
+//   [0..3]          Px_hi - T_x, Py_hi - T_y, Pz_hi - T_z, p (L = 0) or sqrt(p) (L > 0)
+//                   (hi words relative to the tile's reference point T =
+//                   (cx, cy, cz) of its TileMeta; both on the coordinate grid,
+//                   so the difference is exact; FP32 point charges store
+//                   absolute hi words)
 //   [4..7]          Px_lo, Py_lo, Pz_lo, M_0 lo word
 //   [8, 8+n)        M_tuv = (pi/p)^{3/2} D_tuv   (far-field multipole moments)
 //   [8+n]           G_0 lo word
@@ -91,8 +95,9 @@ struct TileMeta {
     int32_t n;        // entries in the tile
     int32_t off32;    // float offset of the first FP32 record (distributions only)
     int32_t off64;    // double offset of the first FP64 record
-    float cx, cy, cz; // bounding-sphere centre (recentred coordinates)
-    float rad;        // bounding-sphere radius
+    float cx, cy, cz; // bounding-sphere centre (recentred coordinates); for distribution
+                      // tiles rounded onto the coordinate grid: the FP32 records' reference point
+    float rad;        // bounding-sphere radius (about that centre)
     float pmin;       // smallest exponent p in the tile (0 for point tiles)
     float qabs;       // sum of absolute charge bounds of the tile's entries
     float vmax;       // largest |Q_d| 2 sqrt(p_d/pi) of an unmerged distribution (0 if none)

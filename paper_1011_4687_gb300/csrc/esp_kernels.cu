@@ -246,11 +246,13 @@ __global__ void __launch_bounds__(kBatchSortThreads) batch_sort_kernel(const Bat
 // ---------------------------------------------------------------------------
 // few positions per call (the paper's call pattern: one r_new per Metropolis
 // move).  The roles of the main kernels turn back to the paper's: threads
-// take environment entries (cells, point charges, distributions), every
-// thread evaluates its entries at all n <= kSmallN positions in FP64, the CTA
-// reduces per position in a fixed order, and CTA b writes partial[b][q].
-// Tiles are dealt round-robin to the CTAs; entries are read straight from the
-// FP64 records (each once per call).
+// take environment entries (cells, point charges, distributions) and evaluate
+// them at the positions of their CTA's chunk (up to kSmallChunk of the n <=
+// kSmallN positions; grid.y = chunk), the CTA reduces per position in a fixed
+// order, and CTA (b, chunk) writes partial[b][q] for its chunk's q.  FP32
+// point charges are read in one flat coalesced pass over their contiguous
+// records (each once per chunk); the other tiles are dealt round-robin to the
+// CTAs of a chunk and read from the FP64 records.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 128;
 
@@ -264,19 +266,24 @@ __device__ __forceinline__ void two_sum_pair(float &s, float &c, float s2, float
     c = (c + c2) + e;
 }
 
-__global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
+__global__ void __launch_bounds__(kSmallThreads, 4) small_n_kernel(SmallArgs a)
 {
-    __shared__ double s_pos[kSmallN][3];
-    __shared__ float s_ph[kSmallN][3], s_pl[kSmallN][3]; // FP32 hi (on the records' grid) and lo words
+    // grid: x = slice of the environment's entries, y = chunk of kSmallChunk
+    // positions; each (slice, position) partial sum is written by one CTA
+    __shared__ double s_pos[kSmallChunk][3];
+    __shared__ float s_ph[kSmallChunk][3], s_pl[kSmallChunk][3]; // FP32 hi (on the records' grid) and lo words
     __shared__ float s_red32[kSmallThreads / 32][kSmallChunk][2];
     __shared__ double s_red64[kSmallThreads / 32][kSmallChunk];
     const int n = a.n_pos;
-    for (int i = threadIdx.x; i < n * 3; i += kSmallThreads) {
-        const double x = a.pos_in[i] - (i % 3 == 0 ? a.cx : i % 3 == 1 ? a.cy : a.cz);
+    const int q0 = blockIdx.y * kSmallChunk;
+    const int nq = min(kSmallChunk, n - q0);
+    for (int i = threadIdx.x; i < nq * 3; i += kSmallThreads) {
+        const int c = i % 3;
+        const double x = a.pos_in[3 * q0 + i] - (c == 0 ? a.cx : c == 1 ? a.cy : a.cz);
         const double h = nearbyint(x / a.quantum) * a.quantum;
-        s_pos[i / 3][i % 3] = x;
-        s_ph[i / 3][i % 3] = float(h);
-        s_pl[i / 3][i % 3] = float(x - h);
+        s_pos[i / 3][c] = x;
+        s_ph[i / 3][c] = float(h);
+        s_pl[i / 3][c] = float(x - h);
     }
     // does this CTA evaluate any entry in FP64?  (then its FP64 sums need a
     // FP64 reduction; FP64 instructions run at 1/64 of the FP32 rate here)
@@ -286,97 +293,91 @@ __global__ void __launch_bounds__(kSmallThreads) small_n_kernel(SmallArgs a)
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gtid = blockIdx.x * kSmallThreads + threadIdx.x, gthreads = gridDim.x * kSmallThreads;
-    for (int q0 = 0; q0 < n; q0 += kSmallChunk) {
-        const int nq = min(kSmallChunk, n - q0);
-        float acc32[kSmallChunk];
-        double acc[kSmallChunk];
+    float acc32[kSmallChunk];
+    double acc[kSmallChunk];
 #pragma unroll
-        for (int q = 0; q < kSmallChunk; ++q) {
-            acc32[q] = 0.0f;
-            acc[q] = 0.0;
+    for (int q = 0; q < kSmallChunk; ++q) {
+        acc32[q] = 0.0f;
+        acc[q] = 0.0;
+    }
+    // FP32 point charges: one flat, coalesced pass over their contiguous
+    // records (thread g takes entries g, g + G, ...: the paper's coalesced
+    // mapping); a thread's few terms sum in FP32
+    if (a.fp32 && a.n_p32 > 0) {
+        for (int e = gtid; e < a.n_p32; e += gthreads) {
+            const float *r = a.rec32 + a.p32_off + (size_t)e * rec32_stride(0);
+            const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
+            const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
+            const float qh = r[rec32_m(0)], ql = r1.w;
+#pragma unroll
+            for (int q = 0; q < kSmallChunk; ++q) {
+                if (q >= nq)
+                    break;
+                const float dx = (r0.x - s_ph[q][0]) + (r1.x - s_pl[q][0]);
+                const float dy = (r0.y - s_ph[q][1]) + (r1.y - s_pl[q][1]);
+                const float dz = (r0.z - s_ph[q][2]) + (r1.z - s_pl[q][2]);
+                const float rs = esp_rsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                acc32[q] += fmaf(qh, rs, ql * rs);
+            }
         }
-        // FP32 point charges: one flat, coalesced pass over their contiguous
-        // records (thread g takes entries g, g + G, ...: the paper's coalesced
-        // mapping); a thread's few terms sum in FP32
-        if (a.fp32 && a.n_p32 > 0) {
-            for (int e = gtid; e < a.n_p32; e += gthreads) {
-                const float *r = a.rec32 + a.p32_off + (size_t)e * rec32_stride(0);
-                const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
-                const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
-                const float qh = r[rec32_m(0)], ql = r1.w;
+    }
+    // every other tile (FP64 points, distributions; FP32 points under FP64),
+    // dealt round-robin to the CTAs, one entry per thread
+    if (has64) {
+        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+            const TileMeta m = a.tiles[t];
+            if (m.cls == kClassPoint32 && a.fp32)
+                continue;
+            const bool pts = is_point_class(m.cls);
+            const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
+            for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
+                const double *r = a.rec64 + m.off64 + (size_t)j * st;
 #pragma unroll
                 for (int q = 0; q < kSmallChunk; ++q) {
                     if (q >= nq)
                         break;
-                    const int k = q0 + q;
-                    const float dx = (r0.x - s_ph[k][0]) + (r1.x - s_pl[k][0]);
-                    const float dy = (r0.y - s_ph[k][1]) + (r1.y - s_pl[k][1]);
-                    const float dz = (r0.z - s_ph[k][2]) + (r1.z - s_pl[k][2]);
-                    const float rs = esp_rsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    acc32[q] += fmaf(qh, rs, ql * rs);
-                }
-            }
-        }
-        // every other tile (FP64 points, distributions; FP32 points under FP64),
-        // dealt round-robin to the CTAs, one entry per thread
-        if (has64) {
-            for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-                const TileMeta m = a.tiles[t];
-                if (m.cls == kClassPoint32 && a.fp32)
-                    continue;
-                const bool pts = is_point_class(m.cls);
-                const int st = pts ? kPointStride64 : rec64_stride(m.cls & 7);
-                for (int j = threadIdx.x; j < m.n; j += kSmallThreads) {
-                    const double *r = a.rec64 + m.off64 + (size_t)j * st;
-#pragma unroll
-                    for (int q = 0; q < kSmallChunk; ++q) {
-                        if (q >= nq)
-                            break;
-                        const int k = q0 + q;
                         if (pts) {
-                            const double dx = r[0] - s_pos[k][0], dy = r[1] - s_pos[k][1], dz = r[2] - s_pos[k][2];
-                            acc[q] += r[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
-                        } else {
-                            acc[q] += tile_f64_one_any(m.cls, r, 1, s_pos[k][0], s_pos[k][1], s_pos[k][2],
-                                                       a.boys64);
-                        }
+                        const double dx = r[0] - s_pos[q][0], dy = r[1] - s_pos[q][1], dz = r[2] - s_pos[q][2];
+                        acc[q] += r[3] * esp_rsqrt(dx * dx + dy * dy + dz * dz);
+                    } else {
+                        acc[q] += tile_f64_one_any(m.cls, r, 1, s_pos[q][0], s_pos[q][1], s_pos[q][2],
+                                                   a.boys64);
                     }
                 }
             }
         }
-        // fixed-order reduction per position: the FP32 sums as (sum,
-        // compensation) pairs by warp shuffles, the FP64 sums (only where this
-        // CTA has any) likewise in FP64, then the warps in order in FP64
+    }
+    // fixed-order reduction per position: the FP32 sums as (sum,
+    // compensation) pairs by warp shuffles, the FP64 sums (only where this
+    // CTA has any) likewise in FP64, then the warps in order in FP64
 #pragma unroll
-        for (int q = 0; q < kSmallChunk; ++q) {
-            if (q >= nq)
-                break;
-            float sv = acc32[q], cv = 0.0f;
-            for (int o = 16; o; o >>= 1) {
-                const float so = __shfl_xor_sync(0xffffffffu, sv, o), co = __shfl_xor_sync(0xffffffffu, cv, o);
-                two_sum_pair(sv, cv, so, co);
-            }
-            double v = 0.0;
-            if (has64) {
-                v = acc[q];
-                for (int o = 16; o; o >>= 1)
-                    v += __shfl_xor_sync(0xffffffffu, v, o);
-            }
-            if (lane == 0) {
-                s_red32[warp][q][0] = sv;
-                s_red32[warp][q][1] = cv;
-                s_red64[warp][q] = v;
-            }
+    for (int q = 0; q < kSmallChunk; ++q) {
+        if (q >= nq)
+            break;
+        float sv = acc32[q], cv = 0.0f;
+        for (int o = 16; o; o >>= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, sv, o), co = __shfl_xor_sync(0xffffffffu, cv, o);
+            two_sum_pair(sv, cv, so, co);
         }
-        __syncthreads();
-        if (threadIdx.x < nq) {
-            double v = 0.0;
-            for (int w = 0; w < kSmallThreads / 32; ++w)
-                v += (double(s_red32[w][threadIdx.x][0]) + double(s_red32[w][threadIdx.x][1])) +
-                     s_red64[w][threadIdx.x];
-            a.partial[(size_t)blockIdx.x * n + q0 + threadIdx.x] = v;
+        double v = 0.0;
+        if (has64) {
+            v = acc[q];
+            for (int o = 16; o; o >>= 1)
+                v += __shfl_xor_sync(0xffffffffu, v, o);
         }
-        __syncthreads(); // the reduction buffers are reused by the next chunk
+        if (lane == 0) {
+            s_red32[warp][q][0] = sv;
+            s_red32[warp][q][1] = cv;
+            s_red64[warp][q] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        double v = 0.0;
+        for (int w = 0; w < kSmallThreads / 32; ++w)
+            v += (double(s_red32[w][threadIdx.x][0]) + double(s_red32[w][threadIdx.x][1])) +
+                 s_red64[w][threadIdx.x];
+        a.partial[(size_t)blockIdx.x * n + q0 + threadIdx.x] = v;
     }
 }
 
@@ -543,13 +544,21 @@ bool batch_shape_supported(int precision, int threads, int ppt)
 #undef ESP_BSHAPE_IS
 }
 
-int small_n_splits(int n_tiles, int num_sms) { return std::max(1, std::min(n_tiles, 8 * num_sms)); }
+// Slices of the environment's entries: about 8 CTAs per SM over all chunks of
+// positions, so that with more positions each thread takes more entries and
+// the per-position reduction is amortised over more terms.
+int small_n_splits(int n_tiles, int num_sms, int n)
+{
+    const int chunks = std::max(1, (n + kSmallChunk - 1) / kSmallChunk);
+    return std::max(1, std::min(n_tiles, 8 * num_sms / chunks));
+}
 
 cudaError_t launch_small_n(const SmallArgs &a, int n_splits, double *V, cudaStream_t s)
 {
     if (a.n_pos <= 0 || a.n_pos > kSmallN)
         return cudaErrorInvalidValue;
-    small_n_kernel<<<n_splits, kSmallThreads, 0, s>>>(a);
+    const dim3 grid(n_splits, (a.n_pos + kSmallChunk - 1) / kSmallChunk);
+    small_n_kernel<<<grid, kSmallThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;

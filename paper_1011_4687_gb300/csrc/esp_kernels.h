@@ -104,13 +104,15 @@ size_t potential_smem_bytes(int precision, int tile_size);
 // FP32C (64,{2,4}), (128,{1,2,4}), (256,{1,2}).
 bool potential_shape_supported(int precision, int threads, int ppt);
 // Few positions per call (n <= kSmallN): environment entries spread over the
-// threads of n_splits CTAs, partial[split][n], then one CTA per position
-// sums the partials into V in a fixed order.  Entries are evaluated in FP64,
-// except the FP32 point charges (class kClassPoint32) when fp32 is set: those
-// take the compensated FP32 form of the main kernel (hi/lo offsets, symmetric
-// rsqrt, low word of the charge) and add into the thread's FP64 sums.
+// threads of n_splits CTAs per chunk of kSmallChunk positions (grid n_splits x
+// chunks), partial[split][n], then one CTA per position sums the partials
+// into V in a fixed order.  Entries are evaluated in FP64, except the FP32
+// point charges (class kClassPoint32) when fp32 is set: those take the
+// compensated FP32 form of the main kernel (hi/lo offsets, symmetric rsqrt,
+// low word of the charge), sum per thread in FP32 and reduce across the CTA
+// as (sum, compensation) pairs before the FP64 partial.
 constexpr int kSmallN = 128;
-constexpr int kSmallChunk = 16;      // positions held in registers per pass
+constexpr int kSmallChunk = 16;      // positions of one CTA, held in registers
 constexpr int kSmallNDistributions = 16; // calls above this many positions take the
                                          // few-position path only for environments of point charges
 struct SmallArgs {
@@ -128,7 +130,7 @@ struct SmallArgs {
     int n_p32;
     double *partial;
 };
-int small_n_splits(int n_tiles, int num_sms);
+int small_n_splits(int n_tiles, int num_sms, int n);
 cudaError_t launch_small_n(const SmallArgs &a, int n_splits, double *V, cudaStream_t s);
 // perm (optional, from launch_sort): V[perm[slot]] receives the sum of slot
 cudaError_t launch_reduce(const double *partial, int n_splits, int n, double *V, cudaStream_t s,

@@ -93,15 +93,17 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         if (m.cls == kClassPoint32) {
             // small point charges: the far form of an L = 0 record, no near path
             const float *s_rec = reinterpret_cast<const float *>(s_tile4);
+            // (absolute hi words: the exact offset form, REL off)
+            const float ct0[3] = {0.0f, 0.0f, 0.0f};
             if constexpr (PPT % 2 == 0) {
                 f2 wq[NP];
-                tile_f32c2<0, NP, true, false, false>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);
+                tile_f32c2<0, NP, true, false, false, false>(s_rec, m.n, ch2, cl2, cl2, ct0, wq, S2, C2, s_boys);
             } else {
                 bool none[PPT];
 #pragma unroll
                 for (int q = 0; q < PPT; ++q)
                     none[q] = false;
-                tile_f32c<0, PPT, true, false, false>(s_rec, m.n, ch, cl, none, S, Cc, s_boys);
+                tile_f32c<0, PPT, true, false, false, false>(s_rec, m.n, ch, cl, cl, ct0, none, S, Cc, s_boys);
             }
             continue;
         }
@@ -129,20 +131,25 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         const bool far = __all_sync(0xffffffffu, lane_far);
         const bool sel = __any_sync(0xffffffffu, any_near); // warp-uniform: any term to select away
         const float *s_rec = reinterpret_cast<const float *>(s_tile4);
+        const float ct[3] = {m.cx, m.cy, m.cz}; // the records' reference point T
         if constexpr (PPT % 2 == 0) {
             // two positions per packed FP32 instruction
-            f2 wq[NP];
+            f2 wq[NP], dq2[NP][3];
 #pragma unroll
-            for (int q = 0; q < NP; ++q)
+            for (int q = 0; q < NP; ++q) {
                 wq[q] = f2(nearq[2 * q] ? 0.0f : 1.0f, nearq[2 * q + 1] ? 0.0f : 1.0f);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    dq2[q][d] = (f2(ct[d]) - ch2[q][d]) - cl2[q][d];
+            }
 #define ESP_TILE(CLS, LL, SH)                                                                   \
     case CLS:                                                                                   \
         if (far && !sel)                                                                        \
-            tile_f32c2<LL, NP, true, SH, false>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);      \
+            tile_f32c2<LL, NP, true, SH, false>(s_rec, m.n, ch2, cl2, dq2, ct, wq, S2, C2, s_boys); \
         else if (far)                                                                           \
-            tile_f32c2<LL, NP, true, SH, true>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);       \
+            tile_f32c2<LL, NP, true, SH, true>(s_rec, m.n, ch2, cl2, dq2, ct, wq, S2, C2, s_boys); \
         else                                                                                    \
-            tile_f32c2<LL, NP, false, SH, true>(s_rec, m.n, ch2, cl2, wq, S2, C2, s_boys);      \
+            tile_f32c2<LL, NP, false, SH, true>(s_rec, m.n, ch2, cl2, dq2, ct, wq, S2, C2, s_boys); \
         break;
             switch (m.cls) {
                 ESP_TILE(0, 0, false)
@@ -159,14 +166,20 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
             }
 #undef ESP_TILE
         } else {
+            float dq[PPT][3];
+#pragma unroll
+            for (int q = 0; q < PPT; ++q)
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    dq[q][d] = (ct[d] - ch[q][d]) - cl[q][d];
 #define ESP_TILE(CLS, LL, SH)                                                                   \
     case CLS:                                                                                   \
         if (far && !sel)                                                                        \
-            tile_f32c<LL, PPT, true, SH, false>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);      \
+            tile_f32c<LL, PPT, true, SH, false>(s_rec, m.n, ch, cl, dq, ct, nearq, S, Cc, s_boys); \
         else if (far)                                                                           \
-            tile_f32c<LL, PPT, true, SH, true>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);       \
+            tile_f32c<LL, PPT, true, SH, true>(s_rec, m.n, ch, cl, dq, ct, nearq, S, Cc, s_boys); \
         else                                                                                    \
-            tile_f32c<LL, PPT, false, SH, true>(s_rec, m.n, ch, cl, nearq, S, Cc, s_boys);      \
+            tile_f32c<LL, PPT, false, SH, true>(s_rec, m.n, ch, cl, dq, ct, nearq, S, Cc, s_boys); \
         break;
             switch (m.cls) {
                 ESP_TILE(0, 0, false)

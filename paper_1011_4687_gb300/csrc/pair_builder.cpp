@@ -638,6 +638,23 @@ esp_status build_environment(const esp_point_charge *charges, int64_t n_charges,
         off32 = out.rec32.size();
         off64 = out.rec64.size();
         bounding_sphere(cbuf.data(), 3, m.n, m);
+        // The tile's reference point T on the coordinate grid (the moved
+        // centre stays inside the sphere grown by 2q), and the records' hi
+        // words stored as Px_hi - T_x: exact, since both lie on the grid and
+        // the difference needs fewer than 24 bits of q.
+        {
+            const double q = out.coord_quantum;
+            const double T[3] = {quantize_hi(m.cx, q), quantize_hi(m.cy, q), quantize_hi(m.cz, q)};
+            m.cx = float(T[0]);
+            m.cy = float(T[1]);
+            m.cz = float(T[2]);
+            m.rad = float(double(m.rad) + 2.0 * q);
+            for (int k = 0; k < m.n; ++k)
+                for (int c = 0; c < 3; ++c) {
+                    float &h = out.rec32[size_t(m.off32) + size_t(k) * st32 + c];
+                    h = float(double(h) - T[c]);
+                }
+        }
         m.pmin = float(pmin);
         m.qabs = float(qsum);
         m.vmax = float(vmax);
