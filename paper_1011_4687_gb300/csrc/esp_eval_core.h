@@ -193,7 +193,7 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
             float F[L + 1];
             if constexpr (FAR) {
                 boys_far<L, float>(dx * dx + dy * dy + dz * dz, F);
-                v = hermite_contract<L, float>(F, dx, dy, dz, K, k0lo);
+                v = hermite_contract<L, float, float, false, true>(F, dx, dy, dz, K, k0lo);
             } else if constexpr (L == 0) {
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 float T = esp_fma(ps, r2, r[rec32_pslo(L)] * r2);
@@ -311,12 +311,12 @@ ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP
                 // the common case: the terms go straight into the block sum
                 const f2 r2 = esp_fma(dx, dx, esp_fma(dy, dy, dz * dz));
                 boys_far<L, f2>(r2, F);
-                blk[q] = hermite_contract<L, f2, float, true>(F, dx, dy, dz, K, k0lo, blk[q]);
+                blk[q] = hermite_contract<L, f2, float, true, true>(F, dx, dy, dz, K, k0lo, blk[q]);
                 continue;
             } else if constexpr (FAR) {
                 const f2 r2 = esp_fma(dx, dx, esp_fma(dy, dy, dz * dz));
                 boys_far<L, f2>(r2, F);
-                v = hermite_contract<L, f2, float>(F, dx, dy, dz, K, k0lo);
+                v = hermite_contract<L, f2, float, false, true>(F, dx, dy, dz, K, k0lo);
             } else if constexpr (L == 0) {
                 const f2 r2 = esp_fma(dx, dx, esp_fma(dy, dy, dz * dz));
                 const f2 T = esp_fma(f2(ps), r2, f2(r[rec32_pslo(L)]) * r2);

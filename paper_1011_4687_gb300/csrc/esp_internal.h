@@ -339,15 +339,18 @@ ESP_HD f2 boys_f0_short(f2 T) { return f2(boys_f0_short<float>(T.x), boys_f0_sho
 // recursion below evaluated at the unscaled offset P - C gives the Cartesian
 // derivatives of 1/|P - C| (the exact potential of a Hermite Gaussian once
 // exp(-p|P-C|^2) is negligible), and the multipole moments M_tuv complete it.
+// Returned pre-multiplied by the recursion's level factor (-2)^n, i.e.
+// F[n] = (-2)^n Fh_n = F[n-1] (-(2n-1)) / r2: the same values as scaling
+// afterwards (powers of two are exact), with fewer multiplications.
 template <int L, typename R>
 ESP_HD void boys_far(R r2, R (&F)[L + 1])
 {
     R rs = esp_rsqrt(r2);
     F[0] = rs;
-    R h = R(0.5) * rs * rs;
+    R h = rs * rs;
 #pragma unroll
     for (int n = 1; n <= L; ++n)
-        F[n] = F[n - 1] * (R(2 * n - 1) * h);
+        F[n] = F[n - 1] * (R(-(2 * n - 1)) * h);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,8 +359,9 @@ ESP_HD void boys_far(R r2, R (&F)[L + 1])
 // ---------------------------------------------------------------------------
 // g0lo is the low word of G_0: the leading product is rounded once with it.
 // With ACC, the terms are added into acc0 (one fewer operation per term than
-// forming the sum and adding it); without, acc0 is ignored.
-template <int L, typename R, typename G_t = R, bool ACC = false>
+// forming the sum and adding it); without, acc0 is ignored.  PRE: F[n] carries
+// the level factor (-2)^n already (boys_far).
+template <int L, typename R, typename G_t = R, bool ACC = false, bool PRE = false>
 ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const G_t *__restrict__ G, G_t g0lo = G_t(0),
                           R acc0 = R(0))
 {
@@ -372,9 +376,11 @@ ESP_HD R hermite_contract(const R (&F)[L + 1], R x, R y, R z, const G_t *__restr
 #pragma unroll
     for (int n = L; n >= 0; --n) {
         R s0 = F[n];
+        if constexpr (!PRE) {
 #pragma unroll
-        for (int k = 0; k < n; ++k)
-            s0 = -R(2) * s0;
+            for (int k = 0; k < n; ++k)
+                s0 = -R(2) * s0;
+        }
         S[n][0] = s0;
 #pragma unroll
         for (int N = 1; N <= L - n; ++N) {
