@@ -198,16 +198,24 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel: str, n_pos: int, kind: str):
-    """DRAM bytes of one launch, from the committed ncu counters of a launch of
-    this workload and size; None if none was taken or the kernel source changed
-    since the capture."""
+    """DRAM bytes of one launch, from the committed ncu counters of this
+    workload; None if none were taken or the kernel source changed since the
+    capture.  An entry holds either the bytes of a launch at this exact size
+    ("positions", "dram_bytes") or, where the full launch is too long to
+    capture, a line through captures at two reduced sizes ("fixed_bytes" +
+    "bytes_per_position" x positions: the environment is read from DRAM about
+    once, the positions' share grows with their number)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
     e = t.get("%s/%s" % (kernel, kind))
-    if not e or e.get("source_hash") != kernel_source_hash() or e.get("positions") != n_pos:
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    if "bytes_per_position" in e:
+        return e["fixed_bytes"] + e["bytes_per_position"] * n_pos
+    if e.get("positions") != n_pos:
         return None
     return e["dram_bytes"]
 

@@ -420,10 +420,10 @@ esp_status esp_surrogate_features(const esp_surrogate *s, float *freq_out, doubl
  * every surrogate value, which the probe must catch. */
 esp_status esp_surrogate_debug_expansion(esp_surrogate *s, double dc, double *coef_out, int32_t max_coef);
 /* Iterations of each bounded wait (mbarrier) of the network's tensor-core
- * kernel before it gives up: the kernel then records an error, waits (with the
- * default limit) for its own copies and MMAs in flight, frees its tensor
- * memory and returns, and the call returns ESP_ERR_TIMEOUT with the context
- * still usable.  limit < 0 restores the default (about one second); 0 makes
+ * kernels (fused inference and the training GEMMs) before it gives up: the
+ * kernel then records an error, waits (with the default limit) for its own
+ * copies and MMAs in flight, frees its tensor memory and returns, and the call
+ * returns ESP_ERR_TIMEOUT with the context still usable.  limit < 0 restores the default (about one second); 0 makes
  * every first wait give up at once (used by the tests of that error path). */
 esp_status esp_surrogate_set_wait_limit(esp_surrogate *s, int32_t limit);
 /* Test hook: the network outputs y [n] (FP32 normalised residual, before the

@@ -95,6 +95,7 @@ struct esp_surrogate {
     DevBuf d_X, d_Z, d_H, d_dZ, d_y, d_dy, d_part, d_t, d_loss;   // per-chunk activations
     DevBuf d_flag, d_pre, d_tot, d_count, d_cpos, d_cidx, d_cV, d_nfail;
     DevBuf d_wpk, d_tcerr, d_ynet;      // packed weights, kernel status, fused-inference outputs
+    DevBuf d_gemmerr;                   // status word of the training GEMMs
     bool packed = false;                // d_wpk holds the current BF16 parameters
     int wait_limit = tc_default_wait_limit(); // bounded waits of the network kernel
     int ynet_cap = 0;
@@ -123,7 +124,8 @@ esp_status ensure_chunk(esp_surrogate *s, int chunk)
         (e = s->d_t.ensure(size_t(chunk) * sizeof(float))) != cudaSuccess ||
         (e = s->d_loss.ensure(size_t(chunk) * sizeof(float) + 64)) != cudaSuccess ||
         (e = s->d_part.ensure(size_t(16) * kHidden * kHidden * sizeof(float) + 256 * (kHidden + 1) * sizeof(float))) !=
-            cudaSuccess)
+            cudaSuccess ||
+        (e = s->d_gemmerr.ensure(16)) != cudaSuccess)
         return cuda_fail(e, "allocating surrogate activations");
     s->chunk_cap = chunk;
     return ESP_OK;
@@ -158,7 +160,7 @@ esp_status forward(esp_surrogate *s, const double *pos, int n, cudaStream_t st)
         g.bias = P + L.b[l];
         g.epi = kEpiSiluFwd;
         g.kchunk = g.K;
-        if ((e = gemm(false, true, g, 1, st)) != cudaSuccess)
+        if ((e = gemm_tc(false, true, g, 1, static_cast<int *>(s->d_gemmerr.p), s->wait_limit, st)) != cudaSuccess)
             return cuda_fail(e, "surrogate forward GEMM");
     }
     return ESP_OK;
@@ -215,7 +217,8 @@ esp_status backward(esp_surrogate *s, int n, cudaStream_t st)
         const int ks = std::min(16, std::max(1, n / 512));
         g.kchunk = ((n + ks - 1) / ks + 31) / 32 * 32;
         const int ksplit = (n + g.kchunk - 1) / g.kchunk;
-        if ((e = gemm(true, false, g, ksplit, st)) != cudaSuccess)
+        if ((e = gemm_tc(true, false, g, ksplit, static_cast<int *>(s->d_gemmerr.p), s->wait_limit, st)) !=
+            cudaSuccess)
             return cuda_fail(e, "surrogate weight-gradient GEMM");
         if ((e = sum_parts(part, ksplit, kHidden * kin, G + L.w[l], st)) != cudaSuccess)
             return cuda_fail(e, "surrogate weight-gradient reduction");
@@ -237,7 +240,8 @@ esp_status backward(esp_surrogate *s, int n, cudaStream_t st)
             h.aux = Z + (l - 1) * act;
             h.epi = kEpiGradSilu;
             h.kchunk = kHidden;
-            if ((e = gemm(false, false, h, 1, st)) != cudaSuccess)
+            if ((e = gemm_tc(false, false, h, 1, static_cast<int *>(s->d_gemmerr.p), s->wait_limit, st)) !=
+                cudaSuccess)
                 return cuda_fail(e, "surrogate input-gradient GEMM");
             std::swap(cur, nxt);
         }
@@ -473,6 +477,23 @@ esp_status net_status(esp_surrogate *s)
     return ESP_OK;
 }
 
+// Status word of the training GEMMs (read after a synchronisation point);
+// cleared for the next pass.
+esp_status gemm_status(esp_surrogate *s)
+{
+    if (!s->d_gemmerr.p)
+        return ESP_OK;
+    int err = 0;
+    cudaError_t e = cudaMemcpy(&err, s->d_gemmerr.p, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && err)
+        e = cudaMemset(s->d_gemmerr.p, 0, 4);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading the training GEMM status");
+    if (err)
+        return fail(ESP_ERR_TIMEOUT, "surrogate training GEMM: a bounded wait gave up");
+    return ESP_OK;
+}
+
 // The far-field approximation (expansion + network) at n device positions:
 // V = (accumulate ? V : 0) + expansion + s y.
 esp_status far_approx(esp_surrogate *s, const double *pos, int n, double *V, bool accumulate, cudaStream_t st)
@@ -506,7 +527,8 @@ void release_sur(esp_surrogate *s)
     DevBuf *bufs[] = {&s->d_params, &s->d_params_bf, &s->d_grad, &s->d_m, &s->d_v, &s->d_coef, &s->d_freq,
                       &s->d_trust, &s->d_X, &s->d_Z, &s->d_H, &s->d_dZ, &s->d_y, &s->d_dy, &s->d_part, &s->d_t,
                       &s->d_loss, &s->d_flag, &s->d_pre, &s->d_tot, &s->d_count, &s->d_cpos, &s->d_cidx, &s->d_cV,
-                      &s->d_nfail, &s->d_wpk, &s->d_tcerr, &s->d_ynet, &s->d_near_tiles, &s->d_far_tiles};
+                      &s->d_nfail, &s->d_wpk, &s->d_tcerr, &s->d_ynet, &s->d_near_tiles, &s->d_far_tiles,
+                      &s->d_gemmerr};
     for (DevBuf *b : bufs)
         b->release();
     for (cudaEvent_t *e : {&s->ev0, &s->ev1, &s->ev2})
@@ -721,6 +743,8 @@ esp_status train(esp_surrogate *s)
     const int B = std::min(cfg.batch, cfg.n_train);
     if ((r = ensure_chunk(s, std::max(B, 1))) != ESP_OK)
         return r;
+    if ((e = cudaMemsetAsync(s->d_gemmerr.p, 0, 4, st)) != cudaSuccess)
+        return cuda_fail(e, "clearing the training GEMM status");
     int step = 0;
     double last_loss = 0.0;
     std::vector<float> lossh(B);
@@ -752,6 +776,10 @@ esp_status train(esp_surrogate *s)
             }
         }
     }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "training the surrogate");
+    if ((r = gemm_status(s)) != ESP_OK)
+        return r;
     s->train_loss = last_loss;
     s->packed = false; // the parameters changed: repack before the next inference
     if ((e = cudaMemcpy(s->params.data(), s->d_params.p, L.total * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
@@ -1066,11 +1094,17 @@ esp_status esp_surrogate_debug_step(esp_surrogate *s, const double *positions, c
         (e = cudaMemcpy(dp.p, positions, size_t(n) * 24, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(dt.p, targets, size_t(n) * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "staging the debug batch");
-    if ((r = ensure_chunk(s, n)) != ESP_OK || (r = forward(s, static_cast<const double *>(dp.p), n, st)) != ESP_OK ||
+    if ((r = ensure_chunk(s, n)) != ESP_OK)
+        return r;
+    if ((e = cudaMemsetAsync(s->d_gemmerr.p, 0, 4, st)) != cudaSuccess)
+        return cuda_fail(e, "clearing the training GEMM status");
+    if ((r = forward(s, static_cast<const double *>(dp.p), n, st)) != ESP_OK ||
         (r = output_layer(s, n, static_cast<const float *>(dt.p), st)) != ESP_OK || (r = backward(s, n, st)) != ESP_OK)
         return r;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "debug step");
+    if ((r = gemm_status(s)) != ESP_OK)
+        return r;
     if (params_out && (e = cudaMemcpy(params_out, s->d_params.p, L.total * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "reading parameters");
     if (grad_out && (e = cudaMemcpy(grad_out, s->d_grad.p, L.total * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)

@@ -3,8 +3,9 @@
 // Network: Fourier features gamma(u) = [sin(2 pi B u), cos(2 pi B u)] of the
 // position u = (r - centre) / R (32 frequencies, 64 features), four hidden
 // layers of 256 with SiLU, one linear output.  BF16 weights and activations,
-// FP32 accumulation on the tensor cores (mma.sync m16n8k16), FP32 master
-// weights updated by Adam.  The network models the residual of the far
+// FP32 accumulation on the tcgen05 tensor cores (training GEMMs in
+// surrogate_gemm.cu, fused inference in surrogate_tc.cu), FP32 master weights
+// updated by Adam.  The network models the residual of the far
 // environment's potential after its FP64 interior solid-harmonic expansion
 // (esp_harmonics.h), so that its BF16 output only carries a small correction.
 #include <cuda_bf16.h>
@@ -20,120 +21,10 @@ namespace sur {
 
 namespace {
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z)
 {
     float s = 1.0f / (1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-
-// C[M x N] = op(A)[M x K] op(B)[K x N] (+ epilogue), 64 x 64 CTA tile, 4 warps
-// of 32 x 32, K in steps of 32.  op(A)[m][k] = A_T ? A[k lda + m] : A[m lda + k],
-// op(B)[k][n] = B_T ? B[n ldb + k] : B[k ldb + n].  grid.z splits K into
-// chunks of kchunk (partial results go to C + z * M * ldc).
-template <bool A_T, bool B_T>
-__global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g)
-{
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD]; // stored [n][k]
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kbeg = blockIdx.z * g.kchunk;
-    const int kend = min(g.K, kbeg + g.kchunk);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                acc[i][j][r] = 0.0f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        for (int e = threadIdx.x; e < BM * BK; e += 128) {
-            int mm = e / BK, kk = e % BK;
-            int m = m0 + mm, k = k0 + kk;
-            __nv_bfloat16 v = zero;
-            if (m < g.M && k < kend)
-                v = A_T ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
-            As[mm][kk] = v;
-        }
-        for (int e = threadIdx.x; e < BN * BK; e += 128) {
-            int nn = e / BK, kk = e % BK;
-            int n = n0 + nn, k = k0 + kk;
-            __nv_bfloat16 v = zero;
-            if (n < g.N && k < kend)
-                v = B_T ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
-            Bs[nn][kk] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + gid;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 2 * tig]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 2 * tig]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 8 + 2 * tig]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 8 + 2 * tig]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + j * 8 + gid;
-                bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][ks + 2 * tig]);
-                bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][ks + 8 + 2 * tig]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_bf16_16816(acc[i][j], af[i], bf[j]);
-        }
-        __syncthreads();
-    }
-    // epilogue
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + 2 * tig + (r & 1);
-                if (m >= g.M || n >= g.N)
-                    continue;
-                float v = acc[i][j][r];
-                const size_t o = (size_t)m * g.ldc + n;
-                switch (g.epi) {
-                case kEpiSiluFwd: { // Z = acc + b; keep Z, emit SiLU(Z)
-                    float z = v + g.bias[n];
-                    if (g.Cf)
-                        g.Cf[o] = z;
-                    g.Cb[o] = __float2bfloat16(silu(z));
-                    break;
-                }
-                case kEpiGradSilu: // dZ_prev = acc * SiLU'(Z_prev)
-                    g.Cb[o] = __float2bfloat16(v * silu_grad(g.aux[o]));
-                    break;
-                default: // raw FP32 (split-K partials)
-                    g.Cf[(size_t)blockIdx.z * g.M * g.ldc + o] = v;
-                }
-            }
-        }
-    }
 }
 
 __global__ void features_kernel(const double *__restrict__ pos, int n, const float *__restrict__ freq, double cx,
@@ -363,20 +254,6 @@ __global__ void scatter_kernel(const double *__restrict__ cV, const int *__restr
 }
 
 } // namespace
-
-cudaError_t gemm(bool a_t, bool b_t, const GemmArgs &g, int ksplit, cudaStream_t s)
-{
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ksplit);
-    if (!a_t && !b_t)
-        gemm_kernel<false, false><<<grid, 128, 0, s>>>(g);
-    else if (!a_t && b_t)
-        gemm_kernel<false, true><<<grid, 128, 0, s>>>(g);
-    else if (a_t && !b_t)
-        gemm_kernel<true, false><<<grid, 128, 0, s>>>(g);
-    else
-        gemm_kernel<true, true><<<grid, 128, 0, s>>>(g);
-    return cudaGetLastError();
-}
 
 cudaError_t features(const double *pos, int n, const float *freq, const double c[3], double inv_r,
                      __nv_bfloat16 *X, cudaStream_t s)

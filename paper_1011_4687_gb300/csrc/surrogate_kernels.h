@@ -30,7 +30,10 @@ struct GemmArgs {
     int kchunk;           // K range of one grid.z slice
 };
 
-cudaError_t gemm(bool a_t, bool b_t, const GemmArgs &g, int ksplit, cudaStream_t s);
+// C = op(A) op(B) with the epilogue g.epi on the tcgen05 tensor cores
+// (surrogate_gemm.cu); N <= 256, grid.z = ksplit slices of g.kchunk.  *err is
+// set to 1 if a bounded wait (wait_limit tries) gave up; C is then not written.
+cudaError_t gemm_tc(bool a_t, bool b_t, const GemmArgs &g, int ksplit, int *err, int wait_limit, cudaStream_t s);
 
 // Fused tcgen05 inference (surrogate_tc.cu).  Offsets (elements) of each
 // layer's weights and biases in the flat parameter vectors, and of each

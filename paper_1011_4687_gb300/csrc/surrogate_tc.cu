@@ -13,11 +13,8 @@
 // the next layer's BF16 operand.  The output layer is a dot product in the
 // last epilogue.  The epilogue is latency-bound, so it runs on 16 warps.
 //
-// Operands use the no-swizzle K-major canonical layout: 8 x 8 BF16 core
-// matrices of 128 contiguous bytes (row r of a core matrix at 16 r bytes);
-// core matrix (i, j) of an R-row operand (rows 8i.., k 8j..) at byte
-// 128 (j R/8 + i), so the stride between core matrices along M/N (SBO) is
-// 128 B and along K (LBO) is 16 R B.  Weights are packed into this layout once
+// Operands use the no-swizzle K-major canonical layout of tc_ptx.h.
+// Weights are packed into this layout once
 // per parameter update (pack_weights_kernel), in chunks of 64 K-columns
 // (32 KB), so each chunk is one contiguous bulk copy.
 //
@@ -28,6 +25,7 @@
 #include <stdint.h>
 
 #include "surrogate_kernels.h"
+#include "tc_ptx.h"
 
 namespace esp {
 namespace sur {
@@ -50,112 +48,28 @@ constexpr int kTmemCols = 256;                   // FP32 accumulator columns (N)
 // or tensor memory outlives the CTA's allocations.
 constexpr int kWaitLimit = 1 << 22;
 
-// Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5),
-// A = B = BF16 (bits 7-9, 10-12), both K-major (bits 15, 16 clear),
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kHidden >> 3) << 17) |
-                            (uint32_t(kRows >> 4) << 24);
+constexpr uint32_t kIdesc = tc::idesc_bf16(kRows, kHidden);
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor: start address, leading (K) and stride
-// (M/N) byte offsets in 16-byte units, the fixed descriptor version 0b001 at
-// bits 46-48, base offset 0, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = uint64_t((saddr >> 4) & 0x3FFFu);
-    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
-    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
-    d |= uint64_t(1) << 46;
-    return d;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit)
-{
-    for (int it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (done)
-            return true;
-    }
-    return false;
-}
-
-// one bulk copy global -> shared, completing `bytes` of transaction on bar
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
+using tc::bulk_load;
+using tc::fence_async_smem;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::mma_commit;
+using tc::operand_off;
+using tc::pack_bf16x2;
+using tc::smem_desc;
+using tc::smem_u32;
+using tc::tmem_ld32;
+__device__ __forceinline__ void tc_fence_before() { tc::fence_before(); }
+__device__ __forceinline__ void tc_fence_after() { tc::fence_after(); }
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
 {
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "setp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-                 "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-        v[i] = __uint_as_float(r[i]);
+    tc::mma_bf16(tmem_d, adesc, bdesc, kIdesc, accumulate);
 }
 
 // SiLU with the fast division (the result is rounded to BF16 or multiplied
 // into an FP32 dot product; a few ulp of FP32 do not reach it)
 __device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
-
-// byte offset of (row, k) in an R-row K-major no-swizzle operand (k % 8 == 0)
-__device__ __forceinline__ uint32_t operand_off(int row, int k, int R)
-{
-    return uint32_t(((k >> 3) * (R >> 3) + (row >> 3)) * 128 + (row & 7) * 16);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
-{
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
 
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_tc_kernel(const double *__restrict__ pos, int n, const float *__restrict__ freq, double cx, double cy,

@@ -5,7 +5,8 @@ if their CUDA call had failed ("alloc", "upload", "graph"); each call must
 return its status, leave its outputs alone, and the next call after the
 variable is cleared must succeed on the same context.  Device side: the
 surrogate network kernel's bounded waits are given a limit of 0, so every
-first wait gives up; the call must return ESP_ERR_TIMEOUT and the context and
+first wait gives up (the fused inference kernel and the training GEMMs); the
+call must return ESP_ERR_TIMEOUT and the context and
 surrogate must work again with the default limit."""
 import os
 
@@ -114,7 +115,16 @@ def test_network_wait_limit_zero_times_out_and_recovers():
             with pytest.raises(esp.EspError) as ei:
                 sur.eval(pos)
             assert ei.value.status == esp.ESP_ERR_TIMEOUT
+            # the training GEMMs (tcgen05) take the same limit
+            tpos = qm_positions(np.random.default_rng(3), 300)
+            tgt = np.random.default_rng(4).normal(size=300).astype(np.float32)
+            with pytest.raises(esp.EspError) as ei:
+                sur.debug_step(tpos, tgt)
+            assert ei.value.status == esp.ESP_ERR_TIMEOUT
             sur.set_wait_limit(-1)
+            _, g1, y1 = sur.debug_step(tpos, tgt)
+            _, g2, y2 = sur.debug_step(tpos, tgt)
+            assert np.all(np.isfinite(g1)) and np.array_equal(g1, g2) and np.array_equal(y1, y2)
             again = sur.predict(pos)
             torch.cuda.synchronize()
             assert torch.equal(again, ref)
