@@ -10,7 +10,7 @@
 namespace esp {
 
 #ifndef ESP_SUM_BLOCK
-#define ESP_SUM_BLOCK 8
+#define ESP_SUM_BLOCK 4
 #endif
 // distributions summed in plain FP32 before a TwoSum into the running pair
 constexpr int kSumBlock = ESP_SUM_BLOCK;
@@ -116,7 +116,7 @@ ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double 
 // one addition per coordinate and term instead of three: the record's part is
 // rounded once relative to T (|P - T| is at most the tile's radius, while the
 // far form needs |P - C| of several radii), and dq once per tile.
-// Terms are summed in FP32 over blocks of kSumBlock (8) distributions and
+// Terms are summed in FP32 over blocks of kSumBlock (4) distributions and
 // each block sum is added into a per-position (S, C) pair by TwoSum.
 // Positions flagged near add nothing here (the caller evaluates the tile for
 // them in FP64).
