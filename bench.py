@@ -421,7 +421,7 @@ def surrogate_leg(args, env, wl, label, torch, stream, flush, exact_ms, V_exact=
            "expansion_only_max_err_ha": info["baseline_max_err"], "expansion_coefficients": info["n_baseline"],
            "steps": len(ms),
            "inference": "FP32C near-tile sum + FP64 solid-harmonic expansion + one fused tcgen05 network kernel; "
-                        "training GEMMs mma.sync"}
+                        "training GEMMs on tcgen05"}
     if V_exact is not None:
         d = (Vs - V_exact).abs()
         res["max_point_diff_vs_exact_fp32c_ha"] = float(d.max().item())

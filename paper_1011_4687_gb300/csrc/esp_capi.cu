@@ -385,24 +385,29 @@ double host_eval_f32c(const esp_ctx *c, const double *C)
         }
         if (m.cls == kClassPoint32) {
             const bool none[1] = {false};
-            const float ct0[3] = {0.0f, 0.0f, 0.0f};
-            tile_f32c<0, 1, true, false, false, false>(c->env.rec32.data() + m.off32, m.n, ch, cl, cl, ct0, none, S,
-                                                       Cc, boys32);
+            float th0[1][3];
+            for (int d = 0; d < 3; ++d)
+                th0[0][d] = 0.0f - ch[0][d];
+            tile_f32c<0, 1, true, false, false>(c->env.rec32.data() + m.off32, m.n, th0, cl, cl, none, S, Cc, boys32);
             continue;
         }
-        bool nearq[1], farq;
-        classify_tile(m, ch[0][0], ch[0][1], ch[0][2], near_r, nearq[0], farq);
+        bool nearq[1], farq, relq;
+        classify_tile(m, ch[0][0], ch[0][1], ch[0][2], near_r, nearq[0], farq, relq);
         const float *r = c->env.rec32.data() + m.off32;
         const float ct[3] = {m.cx, m.cy, m.cz};
-        float dq[1][3];
-        for (int d = 0; d < 3; ++d)
-            dq[0][d] = (ct[d] - ch[0][d]) - cl[0][d];
-#define ESP_TILE(CLS, LL, SH)                                                          \
-    case CLS:                                                                          \
-        if (farq)                                                                      \
-            tile_f32c<LL, 1, true, SH>(r, m.n, ch, cl, dq, ct, nearq, S, Cc, boys32);  \
-        else                                                                           \
-            tile_f32c<LL, 1, false, SH>(r, m.n, ch, cl, dq, ct, nearq, S, Cc, boys32); \
+        float th[1][3], dq[1][3];
+        for (int d = 0; d < 3; ++d) {
+            th[0][d] = ct[d] - ch[0][d];
+            dq[0][d] = th[0][d] - cl[0][d];
+        }
+#define ESP_TILE(CLS, LL, SH)                                                                    \
+    case CLS:                                                                                    \
+        if (relq && !nearq[0])                                                                   \
+            tile_f32c<LL, 1, true, SH, false, true>(r, m.n, th, cl, dq, nearq, S, Cc, boys32);   \
+        else if (farq)                                                                           \
+            tile_f32c<LL, 1, true, SH>(r, m.n, th, cl, dq, nearq, S, Cc, boys32);                \
+        else                                                                                     \
+            tile_f32c<LL, 1, false, SH>(r, m.n, th, cl, dq, nearq, S, Cc, boys32);               \
         break;
         switch (m.cls) {
             ESP_TILE(0, 0, false)

@@ -15,6 +15,13 @@ namespace esp {
 // distributions summed in plain FP32 before a TwoSum into the running pair
 constexpr int kSumBlock = ESP_SUM_BLOCK;
 
+#ifndef ESP_REL_RATIO
+#define ESP_REL_RATIO 8
+#endif
+// far tiles at least this many of their radii away take the one-addition
+// offset (see tile_f32c)
+constexpr float kRelRatio = ESP_REL_RATIO;
+
 // error-free S + x = s + e (Knuth TwoSum); e is added into the compensation C
 ESP_HD void two_sum_acc(float &S, float &C, float x)
 {
@@ -110,12 +117,16 @@ ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double 
 //   offset = (P_hi - C_hi) + (P_lo - C_lo),
 // so that the fixed rounding of stored coordinates does not add up coherently
 // over the electrons of a walker; the leading coefficient carries a low word
-// for the same reason.  REL: the records' hi words are relative to the tile's
-// grid point T (P_hi = stored + T, exact).  The far form then takes
-//   offset = (stored + P_lo) + dq,   dq = (T - C_hi) - C_lo per tile and position,
-// one addition per coordinate and term instead of three: the record's part is
-// rounded once relative to T (|P - T| is at most the tile's radius, while the
-// far form needs |P - C| of several radii), and dq once per tile.
+// for the same reason.  Distribution records store their hi words relative
+// to the tile's grid point T (stored = P_hi - T, exact: both on the grid), and
+// the caller passes th = T - C_hi per position (exact), so the offset is
+//   offset = (stored + th) + (P_lo - C_lo),
+// the same value as above.  REL (far tiles at least kRelRatio radii away):
+//   offset = (stored + P_lo) + dq,   dq = th - C_lo per tile and position,
+// one addition per coordinate and term instead of three.  The record's part is
+// rounded once, the same way for every position (a fixed shift of at most
+// 2^-24 |P - T| <= 2^-24 radius), which is why REL is kept to tiles where
+// that shift is a small fraction of the distance.
 // Terms are summed in FP32 over blocks of kSumBlock (4) distributions and
 // each block sum is added into a per-position (S, C) pair by TwoSum.
 // Positions flagged near add nothing here (the caller evaluates the tile for
@@ -130,10 +141,10 @@ ESP_HD void tile_points_f64(const double *__restrict__ pts, int n, const double 
 // ---------------------------------------------------------------------------
 // SEL: some position may be flagged near (its terms are selected away); a
 // caller that knows none is can drop the select.
-template <int L, int PPT, bool FAR, bool SHORT, bool SEL = true, bool REL = true>
-ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[PPT][3], const float (&cl)[PPT][3],
-                      const float (&dq)[PPT][3], const float (&ct)[3], const bool (&nearq)[PPT], float (&S)[PPT],
-                      float (&Cc)[PPT], const float *__restrict__ s_boys)
+template <int L, int PPT, bool FAR, bool SHORT, bool SEL = true, bool REL = false>
+ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&th)[PPT][3], const float (&cl)[PPT][3],
+                      const float (&dq)[PPT][3], const bool (&nearq)[PPT], float (&S)[PPT], float (&Cc)[PPT],
+                      const float *__restrict__ s_boys)
 {
     constexpr int st = rec32_stride(L);
     constexpr int nh = num_hermite(L);
@@ -147,16 +158,12 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
         const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
         const float ps = r0.w;
         const float plx = r1.x, ply = r1.y, plz = r1.z;
-        // absolute hi words (near form), or the offset from T (far form, REL)
+        // (REL: the record's offset from T, rounded once)
         float px = r0.x, py = r0.y, pz = r0.z;
-        if constexpr (REL && FAR) {
+        if constexpr (REL) {
             px += plx;
             py += ply;
             pz += plz;
-        } else if constexpr (REL) {
-            px += ct[0];
-            py += ct[1];
-            pz += ct[2];
         }
         const float k0lo = FAR ? r1.w : r[c0lo];
         float K[nh];
@@ -181,14 +188,14 @@ ESP_HD void tile_f32c(const float *__restrict__ s_rec, int n, const float (&ch)[
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             float dx, dy, dz;
-            if constexpr (REL && FAR) {
+            if constexpr (REL) {
                 dx = px + dq[q][0];
                 dy = py + dq[q][1];
                 dz = pz + dq[q][2];
             } else {
-                dx = (px - ch[q][0]) + (plx - cl[q][0]);
-                dy = (py - ch[q][1]) + (ply - cl[q][1]);
-                dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+                dx = (px + th[q][0]) + (plx - cl[q][0]);
+                dy = (py + th[q][1]) + (ply - cl[q][1]);
+                dz = (pz + th[q][2]) + (plz - cl[q][2]);
             }
             float v;
             float F[L + 1];
@@ -248,9 +255,9 @@ ESP_HD void two_sum_acc(f2 &S, f2 &C, f2 x)
     C += e;
 }
 
-template <int L, int NP, bool FAR, bool SHORT, bool SEL, bool REL = true>
-ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP][3], const f2 (&cl)[NP][3],
-                       const f2 (&dq)[NP][3], const float (&ct)[3], const f2 (&wq)[NP], f2 (&S)[NP], f2 (&Cc)[NP],
+template <int L, int NP, bool FAR, bool SHORT, bool SEL, bool REL = false>
+ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&th)[NP][3], const f2 (&cl)[NP][3],
+                       const f2 (&dq)[NP][3], const f2 (&wq)[NP], f2 (&S)[NP], f2 (&Cc)[NP],
                        const float *__restrict__ s_boys)
 {
     constexpr int st = rec32_stride(L);
@@ -262,16 +269,12 @@ ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP
         const float4 r0 = reinterpret_cast<const float4 *>(r)[0];
         const float4 r1 = reinterpret_cast<const float4 *>(r)[1];
         const f2 plx(r1.x), ply(r1.y), plz(r1.z);
-        // absolute hi words (near form), or the offset from T (far form, REL)
+        // (REL: the record's offset from T, rounded once)
         float hx = r0.x, hy = r0.y, hz = r0.z;
-        if constexpr (REL && FAR) {
+        if constexpr (REL) {
             hx += r1.x;
             hy += r1.y;
             hz += r1.z;
-        } else if constexpr (REL) {
-            hx += ct[0];
-            hy += ct[1];
-            hz += ct[2];
         }
         const f2 px(hx), py(hy), pz(hz);
         const float ps = r0.w;
@@ -297,14 +300,14 @@ ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             f2 dx, dy, dz;
-            if constexpr (REL && FAR) {
+            if constexpr (REL) {
                 dx = px + dq[q][0];
                 dy = py + dq[q][1];
                 dz = pz + dq[q][2];
             } else {
-                dx = (px - ch[q][0]) + (plx - cl[q][0]);
-                dy = (py - ch[q][1]) + (ply - cl[q][1]);
-                dz = (pz - ch[q][2]) + (plz - cl[q][2]);
+                dx = (px + th[q][0]) + (plx - cl[q][0]);
+                dy = (py + th[q][1]) + (ply - cl[q][1]);
+                dz = (pz + th[q][2]) + (plz - cl[q][2]);
             }
             f2 v;
             f2 F[L + 1];
@@ -358,14 +361,17 @@ ESP_HD void tile_f32c2(const float *__restrict__ s_rec, int n, const f2 (&ch)[NP
 
 // Per-position classification of a tile: near (FP64 instead; only with a
 // positive near_r and for tiles whose distributions can produce potentials
-// above kNearVmax) and far (the asymptotic form is exact to FP32 for every
-// distribution of the tile).
-ESP_HD void classify_tile(const TileMeta &m, float cx, float cy, float cz, float near_r, bool &nearq, bool &farq)
+// above kNearVmax), far (the asymptotic form is exact to FP32 for every
+// distribution of the tile) and rel (far, and at least kRelRatio radii from
+// the tile's sphere: the one-addition offset of tile_f32c applies).
+ESP_HD void classify_tile(const TileMeta &m, float cx, float cy, float cz, float near_r, bool &nearq, bool &farq,
+                          bool &relq)
 {
     float ex = cx - m.cx, ey = cy - m.cy, ez = cz - m.cz;
     float d = sqrtf(ex * ex + ey * ey + ez * ez) - m.rad;
     nearq = near_r > 0.0f && m.vmax >= kNearVmax && d < near_r;
     farq = nearq || (d > 0.0f && m.pmin * d * d >= kBoys32Tmax);
+    relq = nearq || (farq && d >= kRelRatio * m.rad);
 }
 
 } // namespace esp

@@ -15,6 +15,8 @@
 // with p -> infinity gives G_000 F_0 -> q / |P - C|.
 #pragma once
 
+#include <cstring>
+
 #include <math.h>
 #include <stdint.h>
 
@@ -176,6 +178,22 @@ ESP_HD f2 operator*(float a, f2 b) { return f2(a) * b; }
 template <typename R> struct lane_of { using type = R; };
 template <> struct lane_of<f2> { using type = float; };
 
+// y / 2 for a normal positive y by decrementing its exponent: an integer
+// instruction, so it leaves the FP32 pipe to the arithmetic (exact; the
+// reciprocal square roots below are normal for every finite offset)
+ESP_HD float half_normal(float y)
+{
+#if defined(__CUDA_ARCH__)
+    return __int_as_float(__float_as_int(y) - (1 << 23));
+#else
+    uint32_t b;
+    std::memcpy(&b, &y, 4);
+    b -= 1u << 23;
+    std::memcpy(&y, &b, 4);
+    return y;
+#endif
+}
+
 ESP_HD float esp_rsqrt(float x)
 {
 #if defined(__CUDA_ARCH__)
@@ -183,10 +201,11 @@ ESP_HD float esp_rsqrt(float x)
 #else
     float y = 1.0f / sqrtf(x);
 #endif
-    // one Newton step makes the error symmetric about zero (no bias across terms)
+    // one Newton step makes the error symmetric about zero (no bias across
+    // terms): y + (1 - x y^2) y / 2
     float h = x * y;
     float e = fmaf(-h, y, 1.0f);
-    return fmaf(0.5f * e, y, y);
+    return fmaf(e, half_normal(y), y);
 }
 ESP_HD f2 esp_rsqrt(f2 x)
 {
@@ -198,7 +217,7 @@ ESP_HD f2 esp_rsqrt(f2 x)
     // the scalar version's Newton step, both lanes per instruction
     f2 h = x * y;
     f2 e = esp_fma(-h, y, f2(1.0f));
-    return esp_fma(f2(0.5f) * e, y, y);
+    return esp_fma(e, f2(half_normal(y.x), half_normal(y.y)), y);
 }
 ESP_HD double esp_rsqrt(double x)
 {

@@ -93,17 +93,26 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
         if (m.cls == kClassPoint32) {
             // small point charges: the far form of an L = 0 record, no near path
             const float *s_rec = reinterpret_cast<const float *>(s_tile4);
-            // (absolute hi words: the exact offset form, REL off)
-            const float ct0[3] = {0.0f, 0.0f, 0.0f};
+            // (absolute hi words: th = 0 - C_hi, the exact offset form)
             if constexpr (PPT % 2 == 0) {
-                f2 wq[NP];
-                tile_f32c2<0, NP, true, false, false, false>(s_rec, m.n, ch2, cl2, cl2, ct0, wq, S2, C2, s_boys);
+                f2 wq[NP], th2[NP][3];
+#pragma unroll
+                for (int q = 0; q < NP; ++q)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        th2[q][d] = f2(0.0f) - ch2[q][d];
+                tile_f32c2<0, NP, true, false, false>(s_rec, m.n, th2, cl2, cl2, wq, S2, C2, s_boys);
             } else {
                 bool none[PPT];
+                float th[PPT][3];
 #pragma unroll
-                for (int q = 0; q < PPT; ++q)
+                for (int q = 0; q < PPT; ++q) {
                     none[q] = false;
-                tile_f32c<0, PPT, true, false, false, false>(s_rec, m.n, ch, cl, cl, ct0, none, S, Cc, s_boys);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        th[q][d] = 0.0f - ch[q][d];
+                }
+                tile_f32c<0, PPT, true, false, false>(s_rec, m.n, th, cl, cl, none, S, Cc, s_boys);
             }
             continue;
         }
@@ -120,36 +129,42 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
             continue;
         }
         bool nearq[PPT];
-        bool any_near = false, lane_far = true;
+        bool any_near = false, lane_far = true, lane_rel = true;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-            bool f;
-            classify_tile(m, ch[q][0], ch[q][1], ch[q][2], near_r, nearq[q], f);
+            bool f, r;
+            classify_tile(m, ch[q][0], ch[q][1], ch[q][2], near_r, nearq[q], f, r);
             any_near |= nearq[q];
             lane_far &= f;
+            lane_rel &= r;
         }
         const bool far = __all_sync(0xffffffffu, lane_far);
+        const bool rel = __all_sync(0xffffffffu, lane_rel); // implies far
         const bool sel = __any_sync(0xffffffffu, any_near); // warp-uniform: any term to select away
         const float *s_rec = reinterpret_cast<const float *>(s_tile4);
         const float ct[3] = {m.cx, m.cy, m.cz}; // the records' reference point T
         if constexpr (PPT % 2 == 0) {
             // two positions per packed FP32 instruction
-            f2 wq[NP], dq2[NP][3];
+            f2 wq[NP], th2[NP][3], dq2[NP][3];
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 wq[q] = f2(nearq[2 * q] ? 0.0f : 1.0f, nearq[2 * q + 1] ? 0.0f : 1.0f);
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    dq2[q][d] = (f2(ct[d]) - ch2[q][d]) - cl2[q][d];
+                for (int d = 0; d < 3; ++d) {
+                    th2[q][d] = f2(ct[d]) - ch2[q][d];
+                    dq2[q][d] = th2[q][d] - cl2[q][d];
+                }
             }
-#define ESP_TILE(CLS, LL, SH)                                                                   \
-    case CLS:                                                                                   \
-        if (far && !sel)                                                                        \
-            tile_f32c2<LL, NP, true, SH, false>(s_rec, m.n, ch2, cl2, dq2, ct, wq, S2, C2, s_boys); \
-        else if (far)                                                                           \
-            tile_f32c2<LL, NP, true, SH, true>(s_rec, m.n, ch2, cl2, dq2, ct, wq, S2, C2, s_boys); \
-        else                                                                                    \
-            tile_f32c2<LL, NP, false, SH, true>(s_rec, m.n, ch2, cl2, dq2, ct, wq, S2, C2, s_boys); \
+#define ESP_TILE(CLS, LL, SH)                                                                         \
+    case CLS:                                                                                         \
+        if (rel && !sel)                                                                              \
+            tile_f32c2<LL, NP, true, SH, false, true>(s_rec, m.n, th2, cl2, dq2, wq, S2, C2, s_boys); \
+        else if (far && !sel)                                                                         \
+            tile_f32c2<LL, NP, true, SH, false>(s_rec, m.n, th2, cl2, dq2, wq, S2, C2, s_boys);       \
+        else if (far)                                                                                 \
+            tile_f32c2<LL, NP, true, SH, true>(s_rec, m.n, th2, cl2, dq2, wq, S2, C2, s_boys);        \
+        else                                                                                          \
+            tile_f32c2<LL, NP, false, SH, true>(s_rec, m.n, th2, cl2, dq2, wq, S2, C2, s_boys);       \
         break;
             switch (m.cls) {
                 ESP_TILE(0, 0, false)
@@ -166,20 +181,24 @@ __device__ __forceinline__ void cta_f32c(const EvalArgs &a, int bx, int split, f
             }
 #undef ESP_TILE
         } else {
-            float dq[PPT][3];
+            float th[PPT][3], dq[PPT][3];
 #pragma unroll
             for (int q = 0; q < PPT; ++q)
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    dq[q][d] = (ct[d] - ch[q][d]) - cl[q][d];
-#define ESP_TILE(CLS, LL, SH)                                                                   \
-    case CLS:                                                                                   \
-        if (far && !sel)                                                                        \
-            tile_f32c<LL, PPT, true, SH, false>(s_rec, m.n, ch, cl, dq, ct, nearq, S, Cc, s_boys); \
-        else if (far)                                                                           \
-            tile_f32c<LL, PPT, true, SH, true>(s_rec, m.n, ch, cl, dq, ct, nearq, S, Cc, s_boys); \
-        else                                                                                    \
-            tile_f32c<LL, PPT, false, SH, true>(s_rec, m.n, ch, cl, dq, ct, nearq, S, Cc, s_boys); \
+                for (int d = 0; d < 3; ++d) {
+                    th[q][d] = ct[d] - ch[q][d];
+                    dq[q][d] = th[q][d] - cl[q][d];
+                }
+#define ESP_TILE(CLS, LL, SH)                                                                         \
+    case CLS:                                                                                         \
+        if (rel && !sel)                                                                              \
+            tile_f32c<LL, PPT, true, SH, false, true>(s_rec, m.n, th, cl, dq, nearq, S, Cc, s_boys);  \
+        else if (far && !sel)                                                                         \
+            tile_f32c<LL, PPT, true, SH, false>(s_rec, m.n, th, cl, dq, nearq, S, Cc, s_boys);        \
+        else if (far)                                                                                 \
+            tile_f32c<LL, PPT, true, SH, true>(s_rec, m.n, th, cl, dq, nearq, S, Cc, s_boys);         \
+        else                                                                                          \
+            tile_f32c<LL, PPT, false, SH, true>(s_rec, m.n, th, cl, dq, nearq, S, Cc, s_boys);        \
         break;
             switch (m.cls) {
                 ESP_TILE(0, 0, false)

@@ -64,7 +64,7 @@ def test_gradients_match_cpu_reference(torch):
 def _check_fused_network(sur, pos):
     """The fused tcgen05 inference kernel against the CPU reference network
     (FP64 with the kernels' BF16 rounding points) and against the unfused
-    mma.sync forward pass of the training path."""
+    forward pass of the training path (its own tcgen05 GEMMs)."""
     y_tc = sur.debug_net(pos).astype(np.float64)
     params, _, y_mma = sur.debug_step(pos, np.zeros(pos.shape[0], np.float32))
     freq, c, inv_r = sur.features()
