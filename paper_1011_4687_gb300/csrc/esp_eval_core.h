@@ -16,7 +16,7 @@ namespace esp {
 constexpr int kSumBlock = ESP_SUM_BLOCK;
 
 #ifndef ESP_REL_RATIO
-#define ESP_REL_RATIO 8
+#define ESP_REL_RATIO 2
 #endif
 // far tiles at least this many of their radii away take the one-addition
 // offset (see tile_f32c)
