@@ -1,8 +1,9 @@
 // The training GEMMs of the surrogate network on the 5th-generation tensor
 // cores: C = op(A) op(B) (+ the epilogues of GemmArgs), BF16 x BF16 -> FP32.
 //
-// One CTA of 128 threads computes a 128 x BN tile of C (BN = 64 or 256) with
-// its accumulator in tensor memory (BN columns).  K runs in chunks of 64
+// One CTA of 128 threads computes a 128 x BN tile of C (BN = 64, or 256 when
+// that still gives every SM two CTAs) with its accumulator in tensor memory
+// (BN columns).  K runs in chunks of 64
 // through two shared-memory stages: every thread stages one 8 x 8 core matrix
 // of the A chunk (128 rows) and BN / 16 of the B chunk (BN rows) per chunk,
 // loading 8 rows of 16 bytes from global memory and, where the source runs
@@ -250,7 +251,17 @@ cudaError_t gemm_tc(bool a_t, bool b_t, const GemmArgs &g, int ksplit, int *err,
         return cudaSuccess;
     if (g.N > 256 || ksplit < 1 || g.kchunk < 1 || !err || wait_limit < 0)
         return cudaErrorInvalidValue;
-    const bool wide = g.N > 64;
+    // 256-column tiles only when they alone give every SM two CTAs; the
+    // training shapes (8,192-row batches, 256 x 256 weight gradients) take
+    // 64-column tiles and four times the CTAs
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const long long tiles256 = (long long)((g.N + 255) / 256) * ((g.M + kTileM - 1) / kTileM) * ksplit;
+    const bool wide = g.N > 64 && tiles256 >= 2LL * sms;
 #define ESP_TC(AT, BT)                                                                                              \
     return wide ? launch_tc<AT, BT, 256>(g, ksplit, err, wait_limit, s)                                             \
                 : launch_tc<AT, BT, 64>(g, ksplit, err, wait_limit, s)
