@@ -274,7 +274,7 @@ def workload_config(wl, kind: str, units: dict, world: int, reduced: bool = Fals
             "point_charges": int(units["n_point_charges"]), "positions_per_step": n,
             "evals_per_step_per_gpu": int((units["n_distributions"] + units["n_point_charges"]) * n),
             "l2": "inputs larger than L2 (records %s) and L2 flushed between timed steps (512 MB write)"
-                  % ("~1.6 GB" if kind == "large" else "~90 MB"),
+                  % ("~1.7 GB" if kind == "large" else "~90 MB"),
             "parallelism": "replicas (own walkers per GPU, same environment)" if world > 1 else "single GPU"}
 
 
