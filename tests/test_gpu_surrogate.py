@@ -35,16 +35,19 @@ def env_small():
     return small_environment(seed=8801, n_nuclei=60, n_charges=600, n_walkers=4, n_elec=64)
 
 
-def test_gradients_match_cpu_reference(torch):
+@pytest.mark.parametrize("n", [512, 40960])
+def test_gradients_match_cpu_reference(torch, n):
     """Every parameter's gradient against the FP64 reference network with the
     kernels' BF16 rounding points, element by element: |g - g_ref| <= 2e-2 |g_ref|
-    + 2^-8 max|g_ref| of its block (BF16 keeps 8 significant bits)."""
+    + 2^-8 max|g_ref| of its block (BF16 keeps 8 significant bits).  512
+    positions run the tcgen05 GEMMs on 64-column tiles; 40,960 positions (320
+    row tiles) on 256-column tiles for the forward and input-gradient GEMMs."""
     wl = env_small()
     env = esp.Environment(wl.nuclei_xyz, wl.nuclei_Z, wl.pairs)
     with esp.Surrogate(env, n_train=2048, n_valid=512, epochs=0, degree=4) as sur:
         rng = np.random.default_rng(5)
-        pos = qm_positions(rng, 512)
-        t = rng.normal(size=512).astype(np.float32)
+        pos = qm_positions(rng, n)
+        t = rng.normal(size=n).astype(np.float32)
         params, grad, y = sur.debug_step(pos, t)
         freq, c, inv_r = sur.features()
         yr, _ = ref.forward(params.astype(np.float64), freq, c, inv_r, pos, use_bf16=True)
